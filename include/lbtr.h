@@ -1,0 +1,226 @@
+/*
+ * lbtr.h -- C ABI of the GB300 IMEX trust-region library for the discretised
+ * Landau-Brazovskii (LB) model (arXiv 2603.03933).
+ *
+ * Problem (paper §2): on a periodic box with lattice A = diag(L_x, L_y[, L_z]) and a
+ * grid of N = M^d points, minimise
+ *     E(phi) = 1/2 sum_k Lambda_k |phi_hat_k|^2 + (1/N) sum_x F(phi(x)),
+ *     Lambda_k = xi^2 (1 - |Bk|^2)^2,  B = 2 pi A^{-T},
+ *     F(u) = tau/2 u^2 - gamma/6 u^3 + u^4/24,
+ * over zero-mean real fields (the mass constraint, removed by P = [0, I] in §3).
+ * phi_hat is the paper's normalised transform (1/N) sum_x phi(x) e^{-i(Bk).x}.
+ *
+ * Conventions shared by every call:
+ *  - A field is a contiguous array of N real values in row-major order with x
+ *    fastest: [y][x] in 2D, [z][y][x] in 3D.
+ *  - Inner products and norms are the paper's <u,v>_N = (1/N) sum_x u v, which by
+ *    Parseval is the Euclidean metric on the N-1 free Fourier coefficients.
+ *  - Field pointers are DEVICE pointers owned by the caller.  Their element type is
+ *    the context's working type: double for LB_FP64, float for LB_MIXED (except
+ *    lb_imex_tr_solve, whose iterate is always double).  Base addresses must be
+ *    16-byte aligned.
+ *  - Scalar outputs (double*, info structs) are HOST pointers.  Calls that return
+ *    scalars synchronise the given stream before writing them; lb_hessvec only
+ *    enqueues work on the stream and returns.
+ *  - The context owns all scratch memory (allocated in lb_create).  A context is
+ *    not thread-safe: calls on one context must not overlap.
+ *  - No C++ exception crosses this boundary; every call returns an lb_status and
+ *    lb_last_error() describes the last failure of that context.
+ */
+#ifndef LBTR_H
+#define LBTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *lb_stream; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or parameter */
+    LB_ERR_NOT_ZERO_MEAN = 2, /* an input field violates the mass constraint */
+    LB_ERR_NONFINITE = 3,     /* NaN or Inf met in an input or a reduction */
+    LB_ERR_NOCONV = 4,        /* iteration cap reached; outputs hold the last iterate */
+    LB_ERR_TIMEOUT = 5,       /* a device-side grid barrier gave up waiting */
+    LB_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    LB_ERR_OOM = 7,           /* device allocation failed */
+    LB_ERR_UNSUPPORTED = 8    /* grid size or dimension outside what the kernels cover */
+} lb_status;
+
+typedef enum { LB_FP64 = 0, LB_MIXED = 1 } lb_precision;
+/* LB_FP64: every step in double.  LB_MIXED: FFTs, diagonals and the pointwise
+ * updates in float; dot products, norms, the secular equation, the
+ * actual/predicted-reduction ratio and the Lanczos tridiagonal step in double. */
+
+typedef struct {
+    int dim;          /* 2 or 3 */
+    int n;            /* M, points per axis: a power of two, 8..512 (2D) or 8..256 (3D) */
+    double box[3];    /* L_x, L_y, L_z: box lengths (A = diag(box)); box[2] unused in 2D */
+    double xi;        /* Lambda_k = xi^2 (1 - |Bk|^2)^2; xi = 1 is the paper's model */
+    double tau;       /* reduced temperature (eq. lb_energy) */
+    double gamma;     /* three-body coefficient (eq. lb_energy) */
+} lb_problem;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Create a context on the current CUDA device for `prob` in precision `prec`.
+ * Allocates the scratch memory of every call below (a few field-sized buffers).
+ * Errors: LB_ERR_INVALID_ARG (null pointers, non-positive box or n),
+ * LB_ERR_UNSUPPORTED (n not a power of two in range, dim not 2/3), LB_ERR_OOM. */
+lb_status lb_create(const lb_problem *prob, lb_precision prec, lb_ctx **out);
+
+/* Release a context and its scratch memory.  NULL is accepted. */
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Text of the last error of `ctx` (static storage of the context; never NULL). */
+const char *lb_last_error(const lb_ctx *ctx);
+
+/* Bytes of device scratch memory owned by the context. */
+size_t lb_workspace_bytes(const lb_ctx *ctx);
+
+/* Change the model parameters (tau, gamma, xi) of an existing context without
+ * reallocating.  Grid and box are fixed at creation. */
+lb_status lb_set_params(lb_ctx *ctx, double xi, double tau, double gamma);
+
+/*
+ * Energy and gradient (paper §2: eq. interaction_bulk_energy and the gradient
+ * formulas grad G = Lambda Psi_hat, grad F = F_N Gamma F_N^{-1} Psi_hat after it).
+ *   phi    [in]  device field, zero mean.
+ *   energy [out] host double: E(phi) = G + F.
+ *   grad   [out] device field or NULL: g = P[F^{-1} Lambda F phi + F'(phi)].
+ *   gmax   [out] host double or NULL: max_x |g(x)|.
+ * Errors: LB_ERR_NOT_ZERO_MEAN if |mean(phi)| > 1e-10 max(1, rms(phi)) (FP64) or
+ * 1e-5 max(1, rms) (MIXED); LB_ERR_NONFINITE.
+ */
+lb_status lb_energy_grad(lb_ctx *ctx, const void *phi, double *energy, void *grad,
+                         double *gmax, lb_stream stream);
+
+/*
+ * Hessian-vector product (paper §2, grad^2 G = Lambda and grad^2 F = F_N Gamma' F_N^{-1};
+ * §3.2, H = D + T and the remark on computing T d by FFT):
+ *   Hv = P[F^{-1}(Lambda F v) + F''(phi) v],  F''(u) = tau - gamma u + u^2/2.
+ *   phi, v [in]  device fields (v must have zero mean; it is not checked here).
+ *   hv     [out] device field; may not alias phi or v.
+ * Asynchronous: enqueues kernels on `stream` and returns.
+ */
+lb_status lb_hessvec(lb_ctx *ctx, const void *phi, const void *v, void *hv, lb_stream stream);
+
+typedef struct {
+    double eta;        /* IMEX step size (paper §4: 0.1) */
+    double eps_sub;    /* stop when ||g + (H + lambda I) d|| < eps_sub (paper §4: 1e-13) */
+    double rel_tol;    /* also stop when that residual < rel_tol * ||g||; 0 disables */
+    int max_iter;      /* cap on IMEX iterations */
+    int check_every;   /* iterations between host reads of the convergence flag */
+} lb_sub_opts;
+
+typedef struct {
+    int iterations;        /* IMEX iterations performed */
+    int converged;         /* 1 if the residual test passed */
+    double residual;       /* ||g + (H + lambda I) d|| of the returned d */
+    double lambda;         /* Lagrange multiplier of the returned d */
+    double dnorm;          /* ||d|| */
+    double model_value;    /* f(d) = <g,d> + <d,Hd>/2 (eq. tr_subproblem) */
+    long long newton_steps;/* Newton steps spent on the secular equation, summed */
+} lb_sub_info;
+
+/* Fill `o` with the paper's values (eta 0.1, eps_sub 1e-13) and max_iter 20000. */
+void lb_default_sub_opts(lb_sub_opts *o);
+
+/*
+ * Trust-region subproblem min_{||d|| <= r} <g,d> + <d,Hd>/2 (eq. tr_subproblem) by
+ * the adaptive implicit-explicit iteration, Algorithm 3 of §3.2:
+ *   b_k = d_k - eta (g + T d_k),
+ *   lambda_{k+1} = 0 if phi_k(0) <= r^2 else the root of phi_k(lambda) = r^2 by Newton
+ *   (eq. lambda_update_rule), d_{k+1} = (I + eta (D + lambda_{k+1} I))^{-1} b_k.
+ *   phi [in] device field; g [in] device field (zero mean); r > 0.
+ *   d0  [in] device field or NULL: initial point (NULL: d0 = -r g / ||g||, the
+ *       deterministic start of the global-optimality theorem; non-NULL: e.g. the
+ *       randomised start of the hard-case remark, which must satisfy ||d0|| <= r).
+ *   d   [out] device field: the returned d_{k+1}.
+ *   info[out] host struct (may be NULL).
+ * Returns LB_ERR_NOCONV (with d holding the last iterate) if max_iter is reached.
+ */
+lb_status lb_tr_subproblem(lb_ctx *ctx, const void *phi, const void *g, double r,
+                           const void *d0, const lb_sub_opts *opts, void *d,
+                           lb_sub_info *info, lb_stream stream);
+
+typedef struct {
+    int max_steps;     /* Lanczos steps cap (basis vectors kept: max_steps + 1) */
+    double tol;        /* stop when the Ritz residual ||H u - theta u|| <= tol */
+    double sigma;      /* shift of the congruence M = Lambda + sigma; <= 0 picks
+                          max(1e-2, max_x |F''(phi(x))|) */
+    int check_every;   /* Lanczos steps between Rayleigh-Ritz checks */
+    uint64_t seed;     /* seed of the start vector (counter-based Philox4x32-10) */
+} lb_eig_opts;
+
+typedef struct {
+    double lambda_min; /* Rayleigh-Ritz estimate of the smallest eigenvalue of H */
+    double kappa_min;  /* smallest Ritz value of M^{-1/2} H M^{-1/2}: same sign */
+    double residual;   /* ||H u - lambda_min u|| for the unit Ritz vector u */
+    int steps;         /* Lanczos steps taken */
+    int converged;
+} lb_eig_info;
+
+void lb_default_eig_opts(lb_eig_opts *o);
+
+/*
+ * Smallest eigenvalue of the Hessian on zero-mean fields (the SP-II test of the
+ * paper's §1 definition; the eigenvalue diagnostics of §4.1 and §4.3).  The paper
+ * does not state its eigenvalue method; this is Lanczos with full
+ * re-orthogonalisation on K = M^{-1/2} H M^{-1/2}, M = Lambda + sigma (diagonal in
+ * reciprocal space), followed by Rayleigh-Ritz for H on V = M^{-1/2} Q.
+ *   phi [in] device field.   vec [out] device field or NULL: the unit Ritz vector.
+ * Returns LB_ERR_NOCONV if max_steps is reached before tol (results still filled).
+ */
+lb_status lb_lambda_min(lb_ctx *ctx, const void *phi, const lb_eig_opts *opts, void *vec,
+                        lb_eig_info *info, lb_stream stream);
+
+typedef struct {
+    /* Algorithm 1/2 parameters; defaults are the paper's §4 values */
+    double gamma_c, gamma_e, gamma_lam, theta, mu_lo, mu_hi, mu0, r0, nu0;
+    double eps;          /* stop when max_x |g(x)| < eps (paper: 1e-10) */
+    int max_outer;       /* cap on outer iterations */
+    int second_order;    /* 1: also require lambda_min >= -tol2 before returning */
+    double tol2;         /* second-order tolerance */
+    lb_sub_opts sub;     /* inner solver (Algorithm 3) options */
+    lb_eig_opts eig;     /* lambda_min options for the second-order test */
+    int pcg_max_iter;    /* cap on CG iterations of each CONTRACT linear solve */
+    double pcg_rtol;     /* relative tolerance of those solves */
+} lb_tr_opts;
+
+typedef struct {
+    int outer;           /* outer iterations performed */
+    long long inner;     /* IMEX iterations summed over all subproblems */
+    int accepted, contracted, shrunk;
+    double energy;       /* E at the returned iterate */
+    double gmax;         /* max_x |g| at the returned iterate */
+    double lambda_min;   /* last second-order test value (NaN if never run) */
+    int status;          /* lb_status of the solve */
+} lb_tr_info;
+
+void lb_default_tr_opts(lb_tr_opts *o);
+
+/*
+ * IMEX-TR: Algorithm 1 of §3.1 (TRACE outer loop) with CONTRACT (Algorithm 2) and the
+ * subproblem solver above.  phi_inout is a DEVICE array of N doubles in both
+ * precisions (the outer iterate, gradient and ratio test are kept in FP64); in
+ * LB_MIXED the inner iterations run in float.
+ * Returns LB_ERR_NOCONV if max_outer is reached (phi_inout holds the last iterate).
+ */
+lb_status lb_imex_tr_solve(lb_ctx *ctx, double *phi_inout, const lb_tr_opts *opts,
+                           lb_tr_info *info, lb_stream stream);
+
+/* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
+ * (0 restores the default of about two seconds).  Lets tests exercise the
+ * LB_ERR_TIMEOUT path without a hang. */
+lb_status lb_set_barrier_budget(lb_ctx *ctx, long long cycles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBTR_H */
