@@ -1,0 +1,496 @@
+// Pass kernels of the FFT-based LB operators (sm_103a).
+//
+// Storage of a spectrum (internal): the half spectrum of the real-to-complex
+// transform along x is split into
+//   main[rows][H]  complex, kx = 0..H-1 (H = M/2), rows = [z][y] (3D) or [y] (2D)
+//   nyq[rows]      complex, kx = M/2 (the Nyquist plane of the x transform)
+// so that every contiguous run is a power of two.  Entries are unnormalised DFTs;
+// the paper's 1/N is folded into the spectral operations.
+//
+// A d-dimensional transform is a sequence of passes, one per axis:
+//   X pass  (rows of M reals <-> H+1 complex; kernels k_xfwd / k_xinv / k_xmid)
+//   Y pass  (columns along y)  and  Z pass (columns along z): k_cols.
+// The innermost pass (Y in 2D, Z in 3D) sees complete 1-D spectra and applies the
+// reciprocal-space diagonal there (Lambda multiply, the IMEX solve, Parseval sums).
+// The X passes apply the physical-space diagonal and its reductions.
+#pragma once
+#include "common.cuh"
+#include "fft_core.cuh"
+#include "reduce.cuh"
+
+namespace lbtr {
+
+// ------------------------------------------------------------------------------
+// Pointwise model functions F', F'' (paper §2: Gamma, Gamma'), F and F'''.
+// ------------------------------------------------------------------------------
+template <typename T> struct Model { T tau, gamma, eta; };
+
+template <typename T> __device__ __forceinline__ T f0v(const Model<T>& m, T u) {
+    T u2 = u * u;
+    return u2 * (m.tau * (T)0.5 - m.gamma * u * (T)(1.0 / 6.0) + u2 * (T)(1.0 / 24.0));
+}
+template <typename T> __device__ __forceinline__ T f1v(const Model<T>& m, T u) {
+    return u * (m.tau - m.gamma * (T)0.5 * u + u * u * (T)(1.0 / 6.0));
+}
+template <typename T> __device__ __forceinline__ T f2v(const Model<T>& m, T u) {
+    return m.tau - m.gamma * u + (T)0.5 * u * u;
+}
+
+// ------------------------------------------------------------------------------
+// Launch geometry helpers shared by host and device.
+// ------------------------------------------------------------------------------
+__host__ __device__ constexpr int x_nl(int m) { return (m / 2) >= 64 ? 16 : 1024 / (m / 2); }
+__host__ __device__ constexpr int x_nt(int m) { return (m / 2) * x_nl(m) / 8; }
+constexpr int COL_NL = 16;
+__host__ __device__ constexpr int col_nt(int m) { return m * COL_NL / 8 < 32 ? 32 : m * COL_NL / 8; }
+
+template <typename T> __host__ __device__ constexpr size_t x_smem(int m) {
+    return sizeof(cplx<T>) * ((size_t)m + (size_t)(m / 2) * (x_nl(m) + 1) + x_nl(m)) + 128 * sizeof(double);
+}
+template <typename T> __host__ __device__ constexpr size_t col_smem(int m) {
+    return sizeof(cplx<T>) * ((size_t)m + (size_t)m * (COL_NL + 1)) + 3 * (size_t)m * sizeof(T) + 64 * sizeof(double);
+}
+
+// ------------------------------------------------------------------------------
+// X pass, forward: real rows -> spectrum rows (main + nyq), with optional
+// pointwise preprocessing and reductions.
+// ------------------------------------------------------------------------------
+enum XfMode {
+    XF_PLAIN = 0,    // transform in[]
+    XF_HVPMEAN = 1,  // transform in[] = v, reduce sum F''(phi) v
+    XF_ENERGY = 2,   // transform in[] = phi, reduce sum F(phi), sum F'(phi), sum phi, sum phi^2
+    XF_IMEX0 = 3,    // transform b = d - eta (g + F''(phi) d), d = d0[] or dscale * g
+};
+
+template <typename T> struct XfArgs {
+    const T* in;            // field transformed (XF_PLAIN/HVPMEAN/ENERGY)
+    const T* phi;
+    const T* g;
+    const T* d0;            // XF_IMEX0: initial point (may be null)
+    const double* dscale;   // XF_IMEX0 with d0 == null: d = (*dscale) * g
+    cplx<T>* main;
+    cplx<T>* nyq;
+    const cplx<T>* tw;      // W_M table
+    int rows;
+    Model<T> model;
+    RedSlot red;
+    const int* done;        // if non-null and *done != 0: return at once
+};
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(x_nt(M)) k_xfwd(XfArgs<T> a) {
+    constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    using C = cplx<T>;
+    if (a.done && *(volatile const int*)a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + M;
+    C* nyqs = buf + H * LD;
+    double* red = reinterpret_cast<double*>(nyqs + NL);
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+
+    const int row0 = blockIdx.x * NL;
+    constexpr int NQ = (MODE == XF_ENERGY) ? 4 : 1;
+    Acc<T> acc[NQ];
+    T ds = (T)0;
+    if (MODE == XF_IMEX0 && a.d0 == nullptr) ds = (T)(*a.dscale);
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int n = w % H, l = w / H;
+        int row = row0 + l;
+        C z = mk<T>((T)0, (T)0);
+        if (row < a.rows) {
+            size_t idx = (size_t)row * H + n;
+            if (MODE == XF_IMEX0) {
+                C p = reinterpret_cast<const C*>(a.phi)[idx];
+                C gg = reinterpret_cast<const C*>(a.g)[idx];
+                C d = a.d0 ? reinterpret_cast<const C*>(a.d0)[idx] : mk<T>(ds * gg.x, ds * gg.y);
+                z.x = d.x - a.model.eta * (gg.x + f2v(a.model, p.x) * d.x);
+                z.y = d.y - a.model.eta * (gg.y + f2v(a.model, p.y) * d.y);
+            } else {
+                z = reinterpret_cast<const C*>(a.in)[idx];
+                if (MODE == XF_HVPMEAN) {
+                    C p = reinterpret_cast<const C*>(a.phi)[idx];
+                    acc[0].add(f2v(a.model, p.x) * z.x);
+                    acc[0].add(f2v(a.model, p.y) * z.y);
+                } else if (MODE == XF_ENERGY) {
+                    acc[0].add(f0v(a.model, z.x));
+                    acc[0].add(f0v(a.model, z.y));
+                    acc[NQ > 1 ? 1 : 0].add(f1v(a.model, z.x));
+                    acc[NQ > 1 ? 1 : 0].add(f1v(a.model, z.y));
+                    acc[NQ > 2 ? 2 : 0].add(z.x + z.y);
+                    acc[NQ > 3 ? 3 : 0].add(z.x * z.x + z.y * z.y);
+                }
+            }
+        }
+        buf[n * LD + l] = z;
+    }
+    __syncthreads();
+    fft_lines<T, -1, H, NL, NT>(buf, tw, M);
+    r2c_post<T, H, NL, NT>(buf, nyqs, tw, M);
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int k = w % H, l = w / H;
+        int row = row0 + l;
+        if (row < a.rows) a.main[(size_t)row * H + k] = buf[k * LD + l];
+    }
+    for (int l = threadIdx.x; l < NL; l += NT)
+        if (row0 + l < a.rows) a.nyq[row0 + l] = nyqs[l];
+    if (MODE == XF_HVPMEAN || MODE == XF_ENERGY) {
+        double tot[NQ];
+        block_sum<T, NQ>(acc, red, tot);
+        finalize_partials(a.red, tot);
+    }
+}
+
+// ------------------------------------------------------------------------------
+// X pass, inverse: spectrum rows -> real rows, with pointwise postprocessing.
+// ------------------------------------------------------------------------------
+enum XiMode {
+    XI_PLAIN = 0,  // out = x * oscale
+    XI_HVP = 1,    // out = x + F''(phi) v - mean(F'' v)   (mean from msum / N)
+    XI_GRAD = 2,   // out = x + F'(phi) - mean(F'(phi)); reduce max |out|
+};
+
+template <typename T> struct XiArgs {
+    const cplx<T>* main;
+    const cplx<T>* nyq;
+    T* out;
+    const T* phi;
+    const T* v;
+    const double* msum;     // XI_HVP / XI_GRAD: sum whose /N is subtracted
+    double inv_n;
+    T oscale;
+    const cplx<T>* tw;
+    int rows;
+    Model<T> model;
+    RedSlot red;            // XI_GRAD: max |out|
+    const int* done;
+};
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(x_nt(M)) k_xinv(XiArgs<T> a) {
+    constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    using C = cplx<T>;
+    if (a.done && *(volatile const int*)a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + M;
+    C* nyqs = buf + H * LD;
+    double* red = reinterpret_cast<double*>(nyqs + NL);
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    const int row0 = blockIdx.x * NL;
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int k = w % H, l = w / H;
+        int row = row0 + l;
+        buf[k * LD + l] = row < a.rows ? a.main[(size_t)row * H + k] : mk<T>((T)0, (T)0);
+    }
+    for (int l = threadIdx.x; l < NL; l += NT)
+        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : mk<T>((T)0, (T)0);
+    __syncthreads();
+    c2r_pre<T, H, NL, NT>(buf, nyqs, tw, M);
+    fft_lines<T, +1, H, NL, NT>(buf, tw, M);
+    T mean = (T)0;
+    if (MODE != XI_PLAIN) mean = (T)(*a.msum * a.inv_n);
+    double mx = 0.0;
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int n = w % H, l = w / H;
+        int row = row0 + l;
+        if (row >= a.rows) continue;
+        size_t idx = (size_t)row * H + n;
+        C z = buf[n * LD + l];
+        C o;
+        if (MODE == XI_PLAIN) {
+            o = mk<T>(z.x * a.oscale, z.y * a.oscale);
+        } else if (MODE == XI_HVP) {
+            C p = reinterpret_cast<const C*>(a.phi)[idx];
+            C vv = reinterpret_cast<const C*>(a.v)[idx];
+            o.x = z.x + f2v(a.model, p.x) * vv.x - mean;
+            o.y = z.y + f2v(a.model, p.y) * vv.y - mean;
+        } else {
+            C p = reinterpret_cast<const C*>(a.phi)[idx];
+            o.x = z.x + f1v(a.model, p.x) - mean;
+            o.y = z.y + f1v(a.model, p.y) - mean;
+            mx = fmax(mx, fmax(fabs((double)o.x), fabs((double)o.y)));
+        }
+        reinterpret_cast<C*>(a.out)[idx] = o;
+    }
+    if (MODE == XI_GRAD) {
+        double m = block_max(mx, red);
+        finalize_partials(a.red, &m);
+    }
+}
+
+// ------------------------------------------------------------------------------
+// X pass, fused inverse -> pointwise -> forward (spectrum rows in and out).
+// ------------------------------------------------------------------------------
+enum XmMode {
+    XM_IMEX = 0,   // d = x; b = d - eta (g + F''(phi) d)     (Algorithm 3, b_k)
+    XM_TOP = 1,    // y = x; out = F''(phi) y                   (T applied in physical space)
+};
+
+template <typename T> struct XmArgs {
+    cplx<T>* main;          // in and out
+    cplx<T>* nyq;
+    const T* phi;
+    const T* g;
+    const cplx<T>* tw;
+    int rows;
+    T scale;                // applied to x after the inverse transform
+    Model<T> model;
+    const int* done;
+};
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(x_nt(M)) k_xmid(XmArgs<T> a) {
+    constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    using C = cplx<T>;
+    if (a.done && *(volatile const int*)a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + M;
+    C* nyqs = buf + H * LD;
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    const int row0 = blockIdx.x * NL;
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int k = w % H, l = w / H;
+        int row = row0 + l;
+        buf[k * LD + l] = row < a.rows ? a.main[(size_t)row * H + k] : mk<T>((T)0, (T)0);
+    }
+    for (int l = threadIdx.x; l < NL; l += NT)
+        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : mk<T>((T)0, (T)0);
+    __syncthreads();
+    c2r_pre<T, H, NL, NT>(buf, nyqs, tw, M);
+    fft_lines<T, +1, H, NL, NT>(buf, tw, M);
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int n = w % H, l = w / H;
+        int row = row0 + l;
+        C z = buf[n * LD + l];
+        C o = mk<T>((T)0, (T)0);
+        if (row < a.rows) {
+            size_t idx = (size_t)row * H + n;
+            C p = reinterpret_cast<const C*>(a.phi)[idx];
+            T dx = z.x * a.scale, dy = z.y * a.scale;
+            if (MODE == XM_IMEX) {
+                C gg = reinterpret_cast<const C*>(a.g)[idx];
+                o.x = dx - a.model.eta * (gg.x + f2v(a.model, p.x) * dx);
+                o.y = dy - a.model.eta * (gg.y + f2v(a.model, p.y) * dy);
+            } else {
+                o.x = f2v(a.model, p.x) * dx;
+                o.y = f2v(a.model, p.y) * dy;
+            }
+        }
+        buf[n * LD + l] = o;
+    }
+    __syncthreads();
+    fft_lines<T, -1, H, NL, NT>(buf, tw, M);
+    r2c_post<T, H, NL, NT>(buf, nyqs, tw, M);
+    for (int w = threadIdx.x; w < H * NL; w += NT) {
+        int k = w % H, l = w / H;
+        int row = row0 + l;
+        if (row < a.rows) a.main[(size_t)row * H + k] = buf[k * LD + l];
+    }
+    for (int l = threadIdx.x; l < NL; l += NT)
+        if (row0 + l < a.rows) a.nyq[row0 + l] = nyqs[l];
+}
+
+// ------------------------------------------------------------------------------
+// Column passes (Y, Z) with the reciprocal-space operations of the innermost axis.
+// ------------------------------------------------------------------------------
+enum ColMode {
+    C_FWD = 0,       // forward DFT along the column
+    C_INV = 1,       // inverse DFT
+    C_LAM = 2,       // fwd, * Lambda * kscale, zero k = 0, inv         (D of H = D + T)
+    C_LAM_E = 3,     // as C_LAM, also reduce 1/2 sum_k w Lambda |X|^2 * escale  (energy G)
+    C_QUAD_E = 4,    // fwd only, reduce 1/2 sum_k w Lambda |X|^2 * escale (no store)
+    C_IMEX_IN = 5,   // load bsrc, * kscale / (1 + eta (Lambda + lam)), zero k0, inv, store dst
+    C_IMEX_OUT = 6,  // fwd, zero k0, store dst; reduce sum w |bold - X|^2 and sum w |X|^2 (* escale)
+    C_TOP_OUT = 7,   // fwd of T-part, combine out = msc * (Lambda * msc * q + X * kscale), zero k0
+    C_MSCALE_IN = 8, // load q, * msc * kscale, zero k0, inv, store dst
+};
+
+struct ColSeg {
+    int nlines;        // lines in this segment
+    int lgrp;          // line l -> base (l / lgrp) * lhi + (l % lgrp) * llo
+    long long lhi, llo;
+    long long es;      // element stride
+    int elem_contig;   // 1 if es == 1 (load along elements)
+    int kx_const;      // -1: kx = l % H (main); else fixed kx index (nyq: H)
+    int y_div;         // 3D innermost: y index = (l / y_div) ; 2D: 0 (no y line index)
+};
+
+template <typename T> struct ColArgs {
+    cplx<T>* main;           // spectrum the pass transforms (input)
+    cplx<T>* nyq;
+    cplx<T>* dst_main;       // output (C_IMEX_IN / C_IMEX_OUT / C_TOP_OUT / C_MSCALE_IN); else in place
+    cplx<T>* dst_nyq;
+    const cplx<T>* src_main; // C_IMEX_IN: b source; C_IMEX_OUT: b old; C_TOP_OUT/C_MSCALE_IN: q
+    const cplx<T>* src_nyq;
+    const cplx<T>* tw;
+    const T* qtab;           // [3][M] (2 pi / L_a)^2 * wavenum(i)^2 for a = x, y, z
+    ColSeg seg[2];           // main, nyq
+    int nb_main;             // number of blocks of the main segment
+    int dim;
+    T xi2;
+    T kscale;                // multiplier folded into the spectral op (1/N for C_LAM)
+    double escale;           // multiplier of reductions (1/N^2)
+    T eta;
+    T sigma;                 // C_TOP_OUT / C_MSCALE_IN: shift of M = Lambda + sigma
+    const double* lam;       // C_IMEX_IN: device multiplier lambda
+    RedSlot red;
+    const int* done;
+};
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
+    constexpr int NL = COL_NL, NT = col_nt(M), LD = NL + 1, H = M / 2;
+    using C = cplx<T>;
+    if (a.done && *(volatile const int*)a.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + M;
+    T* qt = reinterpret_cast<T*>(buf + M * LD);
+    double* red = reinterpret_cast<double*>(qt + 3 * M);
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    constexpr bool NEED_Q = (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_IN ||
+                             MODE == C_TOP_OUT || MODE == C_MSCALE_IN);
+    if (NEED_Q)
+        for (int i = threadIdx.x; i < 3 * M; i += NT) qt[i] = a.qtab[i];
+
+    const int segi = blockIdx.x < a.nb_main ? 0 : 1;
+    const ColSeg s = a.seg[segi];
+    const int l0 = (segi == 0 ? blockIdx.x : blockIdx.x - a.nb_main) * NL;
+    const C* in_main = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) ? a.src_main : a.main;
+    const C* in_nyq = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) ? a.src_nyq : a.nyq;
+    const C* src = segi == 0 ? in_main : in_nyq;
+    C* dst = (MODE == C_IMEX_IN || MODE == C_IMEX_OUT || MODE == C_TOP_OUT || MODE == C_MSCALE_IN)
+                 ? (segi == 0 ? a.dst_main : a.dst_nyq) : (segi == 0 ? a.main : a.nyq);
+    const C* aux = segi == 0 ? a.src_main : a.src_nyq;   // old b / q for *_OUT modes
+
+    auto addr = [&](int l, int e) -> long long {
+        return (long long)(l / s.lgrp) * s.lhi + (long long)(l % s.lgrp) * s.llo + (long long)e * s.es;
+    };
+    // |Bk|^2 pieces and Hermitian weight of element (l, e) on the innermost axis
+    auto kinfo = [&](int l, int e, T& bk2, T& wgt, bool& is0) {
+        int kx = s.kx_const >= 0 ? s.kx_const : (l % H);
+        T bx = qt[kx];
+        T by, bz;
+        bool zero_other;
+        if (a.dim == 3) {
+            int y = s.kx_const >= 0 ? l : l / H;
+            by = qt[M + y];
+            bz = qt[2 * M + e];
+            zero_other = (y == 0);
+        } else {
+            by = qt[M + e];
+            bz = (T)0;
+            zero_other = true;
+        }
+        bk2 = bx + by + bz;
+        wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
+        is0 = (s.kx_const < 0) && kx == 0 && zero_other && e == 0;
+    };
+
+    // load the tile
+    const int nval = s.nlines - l0 < NL ? s.nlines - l0 : NL;
+    if (s.elem_contig) {
+        for (int w = threadIdx.x; w < M * NL; w += NT) {
+            int e = w % M, l = w / M;
+            buf[e * LD + l] = l < nval ? src[addr(l0 + l, e)] : mk<T>((T)0, (T)0);
+        }
+    } else {
+        for (int w = threadIdx.x; w < M * NL; w += NT) {
+            int l = w % NL, e = w / NL;
+            buf[e * LD + l] = l < nval ? src[addr(l0 + l, e)] : mk<T>((T)0, (T)0);
+        }
+    }
+    __syncthreads();
+
+    constexpr int NQ = (MODE == C_IMEX_OUT) ? 2 : 1;
+    Acc<T> acc[NQ];
+
+    if (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) {
+        T lamv = (MODE == C_IMEX_IN) ? (T)(*a.lam) : (T)0;
+        for (int w = threadIdx.x; w < M * NL; w += NT) {
+            int l = w % NL, e = w / NL;
+            if (l >= nval) continue;
+            T bk2, wgt; bool is0;
+            kinfo(l0 + l, e, bk2, wgt, is0);
+            T t = (T)1 - bk2;
+            T lamk = a.xi2 * t * t;
+            T f;
+            if (MODE == C_IMEX_IN) f = a.kscale / ((T)1 + a.eta * (lamk + lamv));
+            else f = a.kscale / sqrt(lamk + a.sigma);
+            C v = buf[e * LD + l];
+            buf[e * LD + l] = is0 ? mk<T>((T)0, (T)0) : mk<T>(v.x * f, v.y * f);
+        }
+        __syncthreads();
+        fft_lines<T, +1, M, NL, NT>(buf, tw, M);
+    } else if (MODE == C_INV) {
+        fft_lines<T, +1, M, NL, NT>(buf, tw, M);
+    } else {
+        fft_lines<T, -1, M, NL, NT>(buf, tw, M);
+        if (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT || MODE == C_TOP_OUT) {
+            for (int w = threadIdx.x; w < M * NL; w += NT) {
+                int l = w % NL, e = w / NL;
+                if (l >= nval) continue;
+                C v = buf[e * LD + l];
+                T bk2, wgt; bool is0;
+                if (MODE != C_IMEX_OUT) kinfo(l0 + l, e, bk2, wgt, is0);
+                else {
+                    int kx = s.kx_const >= 0 ? s.kx_const : ((l0 + l) % H);
+                    bool zo = (a.dim == 3) ? ((s.kx_const >= 0 ? (l0 + l) : (l0 + l) / H) == 0) : true;
+                    wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
+                    is0 = (s.kx_const < 0) && kx == 0 && zo && e == 0;
+                    bk2 = (T)0;
+                }
+                if (is0) v = mk<T>((T)0, (T)0);
+                if (MODE == C_IMEX_OUT) {
+                    C old = aux[addr(l0 + l, e)];
+                    T dx = old.x - v.x, dy = old.y - v.y;
+                    acc[0].add(wgt * (dx * dx + dy * dy));
+                    acc[NQ - 1].add(wgt * (v.x * v.x + v.y * v.y));
+                    buf[e * LD + l] = v;
+                    continue;
+                }
+                T t = (T)1 - bk2;
+                T lamk = a.xi2 * t * t;
+                if (MODE == C_LAM_E || MODE == C_QUAD_E) acc[0].add((T)0.5 * wgt * lamk * (v.x * v.x + v.y * v.y));
+                if (MODE == C_TOP_OUT) {
+                    C q = aux[addr(l0 + l, e)];
+                    T ms = (T)1 / sqrt(lamk + a.sigma);
+                    T c1 = lamk * ms * ms, c2 = ms * a.kscale;
+                    v = is0 ? mk<T>((T)0, (T)0) : mk<T>(c1 * q.x + c2 * v.x, c1 * q.y + c2 * v.y);
+                } else {
+                    T f = lamk * a.kscale;
+                    v = mk<T>(v.x * f, v.y * f);
+                }
+                buf[e * LD + l] = v;
+            }
+            __syncthreads();
+            if (MODE == C_LAM || MODE == C_LAM_E) fft_lines<T, +1, M, NL, NT>(buf, tw, M);
+        }
+    }
+
+    // store
+    if (MODE != C_QUAD_E) {
+        if (s.elem_contig) {
+            for (int w = threadIdx.x; w < M * NL; w += NT) {
+                int e = w % M, l = w / M;
+                if (l < nval) dst[addr(l0 + l, e)] = buf[e * LD + l];
+            }
+        } else {
+            for (int w = threadIdx.x; w < M * NL; w += NT) {
+                int l = w % NL, e = w / NL;
+                if (l < nval) dst[addr(l0 + l, e)] = buf[e * LD + l];
+            }
+        }
+    }
+    if (MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT) {
+        double tot[NQ];
+        block_sum<T, NQ>(acc, red, tot);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < NQ; ++q) tot[q] *= a.escale;
+        finalize_partials(a.red, tot);
+    }
+}
+
+}  // namespace lbtr

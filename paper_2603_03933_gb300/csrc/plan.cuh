@@ -1,0 +1,133 @@
+// Host-side plan of the FFT-based LB operators for one grid and precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "aux_kernels.cuh"
+#include "passes.cuh"
+
+namespace lbtr {
+
+// Result slots of the reductions (each launch that reduces owns one slot).
+enum Slot {
+    S_HVP = 0,     // sum F''(phi) v
+    S_EF = 1,      // [0] sum F, [1] sum F', [2] sum phi, [3] sum phi^2
+    S_EG = 2,      // G (Parseval sum)
+    S_GMAX = 3,    // max |g|
+    S_IMEX = 4,    // [0] sum w |db|^2 / N^2, [1] sum w |b|^2 / N^2
+    S_RED0 = 5,    // generic physical reductions
+    S_RED1 = 6,
+    S_QUAD = 7,    // G(s) of the ratio test
+    S_COUNT = 8
+};
+constexpr int SLOT_Q = 4;           // quantities per slot
+
+struct Status {
+    int code = 0;
+    std::string msg;
+};
+
+template <typename T>
+class Plan {
+public:
+    using C = cplx<T>;
+    Plan() = default;
+    ~Plan();
+    int init(int dim, int m, const double box[3], double xi, double tau, double gamma, std::string& err);
+    void set_params(double xi, double tau, double gamma);
+
+    // --- operators (all enqueue on `s`) ---
+    // Hv = P[F^{-1} Lambda F v + F''(phi) v]
+    void hessvec(const T* phi, const T* v, T* hv, cudaStream_t s);
+    // energy pieces into slots S_EF (sum F, sum F', sum phi, sum phi^2) and S_EG (G);
+    // gradient into grad (if non-null) and max |g| into S_GMAX
+    void energy_grad(const T* phi, T* grad, cudaStream_t s);
+    // G(s) = 1/2 sum_k Lambda_k |s_hat_k|^2 into S_QUAD
+    void quad_energy(const T* x, cudaStream_t s);
+    // physical reductions into slot (R_DOT: sum x y; R_SUMSQ_MAX; R_SUM_SUMSQ)
+    void phys_reduce(int op, const T* x, const T* y, int slot, cudaStream_t s);
+
+    // --- subproblem (Algorithm 3) ---
+    // Set up b_0 from d0 (or dscale * g) and the first multiplier.
+    int imex_init(const T* phi, const T* g, const T* d0, const double* dscale_dev, double r,
+                  double eps_abs, double eps_rel_abs, int max_iter, cudaStream_t s);
+    // Enqueue iterations j0 .. j0+count-1 (device-side early exit once done).
+    int imex_iterate(const T* phi, const T* g, int j0, int count, cudaStream_t s);
+    // d = F^{-1}(B[final_src] / (1 + eta (Lambda + final_lam)))
+    void imex_final(T* d, cudaStream_t s);
+
+    // --- spectral operators used by Lanczos ---
+    // out = K q with K = M^{-1/2} H M^{-1/2} (q, out paper-normalised half spectra)
+    void kop(const T* phi, const C* q, C* out, double sigma, cudaStream_t s);
+    // x (physical) -> paper-normalised half spectrum
+    void to_spectrum(const T* x, C* out, cudaStream_t s);
+    // paper-normalised half spectrum -> physical; with msc: apply M^{-1/2} first
+    void from_spectrum(const C* q, T* x, bool msc, double sigma, cudaStream_t s);
+
+    // barrier / error bookkeeping
+    void set_barrier_budget(long long cycles) { budget_ = cycles > 0 ? cycles : kDefaultBudget; }
+    int read_error(cudaStream_t s);     // returns and clears the device error flag (sync)
+    // first error returned by a cooperative launch since the last call (then cleared)
+    cudaError_t take_launch_error() { cudaError_t e = launch_err_; launch_err_ = cudaSuccess; return e; }
+    void reset_barrier(cudaStream_t s);
+
+    // accessors
+    const double* slot(int k) const { return d_result_ + k * SLOT_Q; }
+    double* slot_mut(int k) { return d_result_ + k * SLOT_Q; }
+    ImexState* imex_state() { return d_state_; }
+    long long n() const { return n_; }
+    long long spec_len() const { return (long long)rows_ * (h_ + 1); }
+    int m() const { return m_; }
+    int dim() const { return dim_; }
+    int rows() const { return rows_; }
+    size_t bytes() const { return bytes_; }
+    double eta = 0.1;
+    int coop_blocks() const { return coop_blocks_; }
+    const T* qtab() const { return d_qtab_; }
+    T xi2() const { return (T)xi2_; }
+
+    static constexpr long long kDefaultBudget = 4000000000LL;   // ~2 s at 2 GHz
+
+private:
+    void xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
+              C* spec, int slot, cudaStream_t s, const int* done = nullptr);
+    void xinv(int mode, const C* spec, T* out, const T* phi, const T* v, const double* msum, T oscale,
+              int slot, cudaStream_t s, const int* done = nullptr);
+    void xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done = nullptr);
+    void cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
+              const double* lam, int slot, cudaStream_t s, const int* done = nullptr);
+    RedSlot redslot(int slot, int nq, unsigned max_mask);
+    void secular(const C* b, int check, int j, cudaStream_t s);
+
+    int dim_ = 0, m_ = 0, h_ = 0, rows_ = 0;
+    long long n_ = 0;
+    double box_[3] = {0, 0, 0};
+    double xi2_ = 1, tau_ = 0, gamma_ = 0;
+    Model<T> model_{};
+    size_t bytes_ = 0;
+    int coop_blocks_ = 0;
+    long long budget_ = kDefaultBudget;
+    // imex parameters of the current solve
+    double r_ = 0, eps_abs_ = 0, eps_rel_abs_ = 0, rtol_ = 0, steptol_ = 0;
+    int max_iter_ = 0;
+
+    // device memory
+    void* d_base_ = nullptr;
+    C* d_tw_ = nullptr;        // W_M
+    T* d_qtab_ = nullptr;      // [3][M]
+    C* d_work_ = nullptr;      // work spectrum (rows*(H+1))
+    C* d_work2_ = nullptr;     // second work spectrum
+    C* d_b_[2] = {nullptr, nullptr};
+    double* d_partials_ = nullptr;   // per-slot partial sums [S_COUNT][SLOT_Q][max_blocks]
+    double* d_result_ = nullptr;     // [S_COUNT][SLOT_Q]
+    unsigned* d_ticket_ = nullptr;   // [S_COUNT]
+    double* d_secpart_ = nullptr;    // [2][3][coop_blocks]
+    unsigned* d_bar_ = nullptr;      // [2]: count, generation
+    int* d_err_ = nullptr;
+    ImexState* d_state_ = nullptr;
+    int max_blocks_ = 0;
+    cudaError_t launch_err_ = cudaSuccess;
+};
+
+}  // namespace lbtr

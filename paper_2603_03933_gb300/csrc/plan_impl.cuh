@@ -1,0 +1,428 @@
+// Method definitions of Plan<T>; included by the per-precision translation units.
+#pragma once
+#include <cmath>
+#include <cstring>
+
+#include "plan.cuh"
+
+namespace lbtr {
+
+#define LB_CK(call)                                                              \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) { err = std::string(#call) + ": " + cudaGetErrorString(e_); return 6; } \
+    } while (0)
+
+// Dispatch a compile-time grid size M over the supported powers of two.
+#define LB_SWITCH_M(mval, ...)                                      \
+    switch (mval) {                                                 \
+        case 8: { constexpr int M = 8; __VA_ARGS__; } break;        \
+        case 16: { constexpr int M = 16; __VA_ARGS__; } break;      \
+        case 32: { constexpr int M = 32; __VA_ARGS__; } break;      \
+        case 64: { constexpr int M = 64; __VA_ARGS__; } break;      \
+        case 128: { constexpr int M = 128; __VA_ARGS__; } break;    \
+        case 256: { constexpr int M = 256; __VA_ARGS__; } break;    \
+        case 512: { constexpr int M = 512; __VA_ARGS__; } break;    \
+        default: break;                                             \
+    }
+
+template <typename T, int M, int MODE> void launch_xfwd(const XfArgs<T>& a, int grid, cudaStream_t s) {
+    k_xfwd<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+}
+template <typename T, int M, int MODE> void launch_xinv(const XiArgs<T>& a, int grid, cudaStream_t s) {
+    k_xinv<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+}
+template <typename T, int M, int MODE> void launch_xmid(const XmArgs<T>& a, int grid, cudaStream_t s) {
+    k_xmid<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+}
+template <typename T, int M, int MODE> void launch_cols(const ColArgs<T>& a, int grid, cudaStream_t s) {
+    k_cols<T, M, MODE><<<grid, col_nt(M), col_smem<T>(M), s>>>(a);
+}
+
+template <typename T, int M> cudaError_t set_smem_attrs() {
+    cudaError_t e = cudaSuccess;
+    auto setx = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x_smem<T>(M));
+        if (r != cudaSuccess) e = r;
+    };
+    auto setc = [&](const void* f) {
+        cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem<T>(M));
+        if (r != cudaSuccess) e = r;
+    };
+    setx((const void*)k_xfwd<T, M, XF_PLAIN>);
+    setx((const void*)k_xfwd<T, M, XF_HVPMEAN>);
+    setx((const void*)k_xfwd<T, M, XF_ENERGY>);
+    setx((const void*)k_xfwd<T, M, XF_IMEX0>);
+    setx((const void*)k_xinv<T, M, XI_PLAIN>);
+    setx((const void*)k_xinv<T, M, XI_HVP>);
+    setx((const void*)k_xinv<T, M, XI_GRAD>);
+    setx((const void*)k_xmid<T, M, XM_IMEX>);
+    setx((const void*)k_xmid<T, M, XM_TOP>);
+    setc((const void*)k_cols<T, M, C_FWD>);
+    setc((const void*)k_cols<T, M, C_INV>);
+    setc((const void*)k_cols<T, M, C_LAM>);
+    setc((const void*)k_cols<T, M, C_LAM_E>);
+    setc((const void*)k_cols<T, M, C_QUAD_E>);
+    setc((const void*)k_cols<T, M, C_IMEX_IN>);
+    setc((const void*)k_cols<T, M, C_IMEX_OUT>);
+    setc((const void*)k_cols<T, M, C_TOP_OUT>);
+    setc((const void*)k_cols<T, M, C_MSCALE_IN>);
+    return e;
+}
+
+template <typename T> Plan<T>::~Plan() {
+    if (d_base_) cudaFree(d_base_);
+}
+
+template <typename T>
+int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, double gamma, std::string& err) {
+    dim_ = dim; m_ = m; h_ = m / 2;
+    rows_ = dim == 3 ? m * m : m;
+    n_ = (long long)rows_ * m;
+    for (int i = 0; i < 3; ++i) box_[i] = box[i];
+    set_params(xi, tau, gamma);
+
+    int dev = 0, nsm = 0;
+    LB_CK(cudaGetDevice(&dev));
+    LB_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaError_t ea = cudaSuccess;
+    LB_SWITCH_M(m_, ea = set_smem_attrs<T, M>());
+    if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+
+    int occ = 0;
+    LB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_secular<T>, 256, 3 * m_ * sizeof(T)));
+    if (occ < 1) occ = 1;
+    coop_blocks_ = nsm * occ;
+    if (coop_blocks_ > 4 * nsm) coop_blocks_ = 4 * nsm;
+
+    int gx = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    int gc = (int)((((long long)rows_ * h_) + COL_NL - 1) / COL_NL + (rows_ + COL_NL - 1) / COL_NL);
+    max_blocks_ = std::max(std::max(gx, gc), std::max(coop_blocks_, 8 * nsm));
+
+    const long long sl = spec_len();
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+    size_t o_tw = take(sizeof(C) * m_);
+    size_t o_q = take(sizeof(T) * 3 * m_);
+    size_t o_w = take(sizeof(C) * sl);
+    size_t o_w2 = take(sizeof(C) * sl);
+    size_t o_b0 = take(sizeof(C) * sl);
+    size_t o_b1 = take(sizeof(C) * sl);
+    size_t o_p = take(sizeof(double) * S_COUNT * SLOT_Q * (size_t)max_blocks_);
+    size_t o_r = take(sizeof(double) * S_COUNT * SLOT_Q);
+    size_t o_t = take(sizeof(unsigned) * S_COUNT);
+    size_t o_sp = take(sizeof(double) * 2 * 3 * (size_t)coop_blocks_);
+    size_t o_bar = take(sizeof(unsigned) * 2);
+    size_t o_err = take(sizeof(int));
+    size_t o_st = take(sizeof(ImexState));
+    bytes_ = off;
+    cudaError_t ma = cudaMalloc(&d_base_, bytes_);
+    if (ma != cudaSuccess) { err = "cudaMalloc of the plan workspace failed"; d_base_ = nullptr; return 7; }
+    char* b = static_cast<char*>(d_base_);
+    d_tw_ = reinterpret_cast<C*>(b + o_tw);
+    d_qtab_ = reinterpret_cast<T*>(b + o_q);
+    d_work_ = reinterpret_cast<C*>(b + o_w);
+    d_work2_ = reinterpret_cast<C*>(b + o_w2);
+    d_b_[0] = reinterpret_cast<C*>(b + o_b0);
+    d_b_[1] = reinterpret_cast<C*>(b + o_b1);
+    d_partials_ = reinterpret_cast<double*>(b + o_p);
+    d_result_ = reinterpret_cast<double*>(b + o_r);
+    d_ticket_ = reinterpret_cast<unsigned*>(b + o_t);
+    d_secpart_ = reinterpret_cast<double*>(b + o_sp);
+    d_bar_ = reinterpret_cast<unsigned*>(b + o_bar);
+    d_err_ = reinterpret_cast<int*>(b + o_err);
+    d_state_ = reinterpret_cast<ImexState*>(b + o_st);
+    LB_CK(cudaMemset(d_base_, 0, bytes_));
+
+    // twiddles W_M^j = exp(-2 pi i j / M), evaluated in long double on the host
+    std::vector<C> tw(m_);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int j = 0; j < m_; ++j) {
+        long double ang = -2.0L * pi * (long double)j / (long double)m_;
+        tw[j] = mk<T>((T)cosl(ang), (T)sinl(ang));
+    }
+    // |Bk|^2 per axis: (2 pi / L_a)^2 k^2 with the signed wavenumber of each index
+    std::vector<T> q(3 * m_, (T)0);
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dim_) break;
+        long double c = 2.0L * pi / (long double)box_[a];
+        for (int i = 0; i < m_; ++i) {
+            int k = i < m_ / 2 ? i : i - m_;
+            q[a * m_ + i] = (T)(c * c * (long double)k * (long double)k);
+        }
+    }
+    LB_CK(cudaMemcpy(d_tw_, tw.data(), sizeof(C) * m_, cudaMemcpyHostToDevice));
+    LB_CK(cudaMemcpy(d_qtab_, q.data(), sizeof(T) * 3 * m_, cudaMemcpyHostToDevice));
+    return 0;
+}
+
+template <typename T> void Plan<T>::set_params(double xi, double tau, double gamma) {
+    xi2_ = xi * xi; tau_ = tau; gamma_ = gamma;
+    model_.tau = (T)tau; model_.gamma = (T)gamma; model_.eta = (T)eta;
+}
+
+template <typename T> RedSlot Plan<T>::redslot(int slot, int nq, unsigned max_mask) {
+    RedSlot r;
+    r.partials = d_partials_ + (size_t)slot * SLOT_Q * max_blocks_;
+    r.result = d_result_ + slot * SLOT_Q;
+    r.ticket = d_ticket_ + slot;
+    r.nq = nq;
+    r.max_mask = max_mask;
+    return r;
+}
+
+template <typename T>
+void Plan<T>::xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
+                   C* spec, int slot, cudaStream_t s, const int* done) {
+    XfArgs<T> a;
+    a.in = in; a.phi = phi; a.g = g; a.d0 = d0; a.dscale = dscale;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.tw = d_tw_; a.rows = rows_; a.model = model_; a.model.eta = (T)eta;
+    a.red = redslot(slot, mode == XF_ENERGY ? 4 : 1, 0u);
+    a.done = done;
+    int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    LB_SWITCH_M(m_, {
+        if (mode == XF_PLAIN) launch_xfwd<T, M, XF_PLAIN>(a, grid, s);
+        else if (mode == XF_HVPMEAN) launch_xfwd<T, M, XF_HVPMEAN>(a, grid, s);
+        else if (mode == XF_ENERGY) launch_xfwd<T, M, XF_ENERGY>(a, grid, s);
+        else launch_xfwd<T, M, XF_IMEX0>(a, grid, s);
+    });
+}
+
+template <typename T>
+void Plan<T>::xinv(int mode, const C* spec, T* out, const T* phi, const T* v, const double* msum, T oscale,
+                   int slot, cudaStream_t s, const int* done) {
+    XiArgs<T> a;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.out = out; a.phi = phi; a.v = v; a.msum = msum; a.inv_n = 1.0 / (double)n_; a.oscale = oscale;
+    a.tw = d_tw_; a.rows = rows_; a.model = model_;
+    a.red = redslot(slot, 1, 1u);
+    a.done = done;
+    int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    LB_SWITCH_M(m_, {
+        if (mode == XI_PLAIN) launch_xinv<T, M, XI_PLAIN>(a, grid, s);
+        else if (mode == XI_HVP) launch_xinv<T, M, XI_HVP>(a, grid, s);
+        else launch_xinv<T, M, XI_GRAD>(a, grid, s);
+    });
+}
+
+template <typename T>
+void Plan<T>::xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done) {
+    XmArgs<T> a;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.phi = phi; a.g = g; a.tw = d_tw_; a.rows = rows_; a.scale = scale;
+    a.model = model_; a.model.eta = (T)eta;
+    a.done = done;
+    int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    LB_SWITCH_M(m_, {
+        if (mode == XM_IMEX) launch_xmid<T, M, XM_IMEX>(a, grid, s);
+        else launch_xmid<T, M, XM_TOP>(a, grid, s);
+    });
+}
+
+// axis: 1 = Y, 2 = Z
+template <typename T>
+void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
+                   const double* lam, int slot, cudaStream_t s, const int* done) {
+    ColArgs<T> a;
+    const long long M = m_, H = h_;
+    a.main = spec; a.nyq = spec ? spec + (size_t)rows_ * h_ : nullptr;
+    a.dst_main = dst; a.dst_nyq = dst ? dst + (size_t)rows_ * h_ : nullptr;
+    a.src_main = src; a.src_nyq = src ? src + (size_t)rows_ * h_ : nullptr;
+    a.tw = d_tw_; a.qtab = d_qtab_;
+    ColSeg s0{}, s1{};
+    if (dim_ == 3 && axis == 1) {
+        s0 = ColSeg{(int)(M * H), (int)H, M * H, 1, H, 0, -1, 0};
+        s1 = ColSeg{(int)M, 1, M, 0, 1, 1, (int)H, 0};
+    } else if (dim_ == 3) {
+        s0 = ColSeg{(int)(M * H), (int)(M * H), 0, 1, M * H, 0, -1, 0};
+        s1 = ColSeg{(int)M, (int)M, 0, 1, M, 0, (int)H, 0};
+    } else {
+        s0 = ColSeg{(int)H, (int)H, 0, 1, H, 0, -1, 0};
+        s1 = ColSeg{1, 1, 0, 0, 1, 1, (int)H, 0};
+    }
+    a.seg[0] = s0; a.seg[1] = s1;
+    a.nb_main = (s0.nlines + COL_NL - 1) / COL_NL;
+    int grid = a.nb_main + (s1.nlines + COL_NL - 1) / COL_NL;
+    a.dim = dim_; a.xi2 = (T)xi2_; a.kscale = kscale; a.escale = escale; a.eta = (T)eta;
+    a.sigma = (T)sigma; a.lam = lam;
+    a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : 1, 0u);
+    a.done = done;
+    LB_SWITCH_M(m_, {
+        switch (mode) {
+            case C_FWD: launch_cols<T, M, C_FWD>(a, grid, s); break;
+            case C_INV: launch_cols<T, M, C_INV>(a, grid, s); break;
+            case C_LAM: launch_cols<T, M, C_LAM>(a, grid, s); break;
+            case C_LAM_E: launch_cols<T, M, C_LAM_E>(a, grid, s); break;
+            case C_QUAD_E: launch_cols<T, M, C_QUAD_E>(a, grid, s); break;
+            case C_IMEX_IN: launch_cols<T, M, C_IMEX_IN>(a, grid, s); break;
+            case C_IMEX_OUT: launch_cols<T, M, C_IMEX_OUT>(a, grid, s); break;
+            case C_TOP_OUT: launch_cols<T, M, C_TOP_OUT>(a, grid, s); break;
+            default: launch_cols<T, M, C_MSCALE_IN>(a, grid, s); break;
+        }
+    });
+}
+
+template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    xfwd(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    cols(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0, s);
+    if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    xinv(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
+}
+
+template <typename T> void Plan<T>::energy_grad(const T* phi, T* grad, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    const double inv_n = 1.0 / (double)n_;
+    xfwd(XF_ENERGY, phi, phi, nullptr, nullptr, nullptr, d_work_, S_EF, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    if (grad) {
+        cols(inner, C_LAM_E, d_work_, nullptr, nullptr, (T)inv_n, inv_n * inv_n, 0.0, nullptr, S_EG, s);
+        if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+        xinv(XI_GRAD, d_work_, grad, phi, nullptr, slot(S_EF) + 1, (T)1, S_GMAX, s);
+    } else {
+        cols(inner, C_QUAD_E, d_work_, nullptr, nullptr, (T)1, inv_n * inv_n, 0.0, nullptr, S_EG, s);
+    }
+}
+
+template <typename T> void Plan<T>::quad_energy(const T* x, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    const double inv_n = 1.0 / (double)n_;
+    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work_, S_RED0, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    cols(inner, C_QUAD_E, d_work_, nullptr, nullptr, (T)1, inv_n * inv_n, 0.0, nullptr, S_QUAD, s);
+}
+
+template <typename T> void Plan<T>::phys_reduce(int op, const T* x, const T* y, int slot, cudaStream_t s) {
+    PhysRedArgs<T> a;
+    a.x = x; a.y = y; a.n = n_;
+    int grid = (int)std::min<long long>(max_blocks_, (n_ + 255) / 256);
+    if (grid < 1) grid = 1;
+    if (op == R_DOT) {
+        a.red = redslot(slot, 1, 0u);
+        k_physred<T, R_DOT><<<grid, 256, 0, s>>>(a);
+    } else if (op == R_SUMSQ_MAX) {
+        a.red = redslot(slot, 2, 2u);
+        k_physred<T, R_SUMSQ_MAX><<<grid, 256, 0, s>>>(a);
+    } else {
+        a.red = redslot(slot, 2, 0u);
+        k_physred<T, R_SUM_SUMSQ><<<grid, 256, 0, s>>>(a);
+    }
+}
+
+template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaStream_t s) {
+    SecArgs<T> a;
+    a.bmain = b; a.bnyq = b + (size_t)rows_ * h_;
+    a.qtab = d_qtab_;
+    a.res = slot(S_IMEX);
+    a.st = d_state_;
+    a.partials = d_secpart_;
+    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 1; a.bar.err = d_err_; a.bar.budget = budget_;
+    a.dim = dim_; a.m = m_; a.rows = rows_;
+    a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
+    a.eta = eta; a.r = r_; a.rtol = rtol_; a.steptol = steptol_;
+    a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_;
+    a.check = check; a.max_iter = max_iter_;
+    a.xi2 = (T)xi2_;
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_secular<T>, dim3(coop_blocks_), dim3(256), args,
+                                                3 * m_ * sizeof(T), s);
+    if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+}
+
+template <typename T>
+int Plan<T>::imex_init(const T* phi, const T* g, const T* d0, const double* dscale_dev, double r,
+                       double eps_abs, double eps_rel_abs, int max_iter, cudaStream_t s) {
+    r_ = r; eps_abs_ = eps_abs; eps_rel_abs_ = eps_rel_abs; max_iter_ = max_iter;
+    rtol_ = sizeof(T) == 8 ? 1e-13 : 2e-6;
+    steptol_ = sizeof(T) == 8 ? 1e-15 : 1e-8;
+    model_.eta = (T)eta;
+    const int inner = dim_ == 3 ? 2 : 1;
+    cudaMemsetAsync(d_state_, 0, sizeof(ImexState), s);
+    cudaMemsetAsync(d_b_[1], 0, sizeof(C) * spec_len(), s);
+    xfwd(XF_IMEX0, nullptr, phi, g, d0, dscale_dev, d_work_, S_RED0, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    const double inv_n = 1.0 / (double)n_;
+    cols(inner, C_IMEX_OUT, d_work_, d_b_[0], d_b_[1], (T)1, inv_n * inv_n, 0.0, nullptr, S_IMEX, s);
+    secular(d_b_[0], 0, 0, s);
+    return 0;
+}
+
+template <typename T> int Plan<T>::imex_iterate(const T* phi, const T* g, int j0, int count, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    const double inv_n = 1.0 / (double)n_;
+    const int* done = &d_state_->done;
+    for (int j = j0; j < j0 + count; ++j) {
+        C* src = d_b_[(j - 1) & 1];
+        C* dst = d_b_[j & 1];
+        cols(inner, C_IMEX_IN, nullptr, d_work_, src, (T)inv_n, 0.0, 0.0, &d_state_->lam, S_RED0, s, done);
+        if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        xmid(XM_IMEX, d_work_, phi, g, (T)1, s, done);
+        if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        cols(inner, C_IMEX_OUT, d_work_, dst, src, (T)1, inv_n * inv_n, 0.0, nullptr, S_IMEX, s, done);
+        secular(dst, 1, j, s);
+    }
+    return 0;
+}
+
+template <typename T> void Plan<T>::imex_final(T* d, cudaStream_t s) {
+    // caller has synchronised and knows final_src via the state
+    ImexState st;
+    cudaMemcpyAsync(&st, d_state_, sizeof(ImexState), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    const int inner = dim_ == 3 ? 2 : 1;
+    const double inv_n = 1.0 / (double)n_;
+    cols(inner, C_IMEX_IN, nullptr, d_work_, d_b_[st.final_src & 1], (T)inv_n, 0.0, 0.0, &d_state_->final_lam,
+         S_RED0, s);
+    if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    xinv(XI_PLAIN, d_work_, d, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+}
+
+template <typename T> void Plan<T>::to_spectrum(const T* x, C* out, cudaStream_t s) {
+    // paper-normalised coefficients: DFT / N
+    const int inner = dim_ == 3 ? 2 : 1;
+    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, out, S_RED0, s);
+    if (dim_ == 3) cols(1, C_FWD, out, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    cols(inner, C_FWD, out, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    long long len = spec_len() * 2;
+    k_axpby<T><<<(int)std::min<long long>(4096, (len + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<T*>(out), reinterpret_cast<const T*>(out), 1.0 / (double)n_, 0.0, nullptr, 0.0, len);
+}
+
+template <typename T> void Plan<T>::from_spectrum(const C* q, T* x, bool msc, double sigma, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    if (msc) {
+        cols(inner, C_MSCALE_IN, nullptr, d_work2_, q, (T)1, 0.0, sigma, nullptr, S_RED0, s);
+    } else {
+        cudaMemcpyAsync(d_work2_, q, sizeof(C) * spec_len(), cudaMemcpyDeviceToDevice, s);
+        cols(inner, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    }
+    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    xinv(XI_PLAIN, d_work2_, x, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+}
+
+template <typename T> void Plan<T>::kop(const T* phi, const C* q, C* out, double sigma, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    cols(inner, C_MSCALE_IN, nullptr, d_work2_, q, (T)1, 0.0, sigma, nullptr, S_RED0, s);
+    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    xmid(XM_TOP, d_work2_, phi, nullptr, (T)1, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    cols(inner, C_TOP_OUT, d_work2_, out, q, (T)(1.0 / (double)n_), 0.0, sigma, nullptr, S_RED0, s);
+}
+
+template <typename T> int Plan<T>::read_error(cudaStream_t s) {
+    int e = 0;
+    cudaMemcpyAsync(&e, d_err_, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (e) reset_barrier(s);
+    return e;
+}
+
+template <typename T> void Plan<T>::reset_barrier(cudaStream_t s) {
+    cudaMemsetAsync(d_bar_, 0, 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(d_err_, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+}
+
+}  // namespace lbtr

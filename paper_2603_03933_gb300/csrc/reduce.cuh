@@ -1,0 +1,180 @@
+// Reductions for the LB kernels.
+//
+// Dot products, norms and energies are always accumulated to double accuracy.  On
+// GB300 double-precision arithmetic runs at a small fraction of the float rate, so
+// the float path accumulates in "double-float" form (an unevaluated sum hi + lo of
+// two floats, each addition done with Knuth's error-free TwoSum), reduces warps and
+// blocks in that form, and converts to double once per block.  The double path
+// accumulates in double.  Block results go to a per-launch partials array; the last
+// block to finish (atomic ticket) sums them in index order, so results are
+// deterministic run to run.
+#pragma once
+#include "common.cuh"
+
+namespace lbtr {
+
+struct ff { float hi, lo; };
+
+// TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    s.lo += a.lo;
+    return two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return two_sum(s.hi, s.lo);
+}
+
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double v;
+    __device__ __forceinline__ Acc() : v(0.0) {}
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add_shfl(int off) { v += __shfl_down_sync(0xffffffffu, v, off); }
+    __device__ __forceinline__ double get() const { return v; }
+    __device__ __forceinline__ void merge(const Acc& o) { v += o.v; }
+};
+template <> struct Acc<float> {
+    ff v;
+    __device__ __forceinline__ Acc() { v.hi = 0.f; v.lo = 0.f; }
+    __device__ __forceinline__ void add(float x) { v = ff_add(v, x); }
+    __device__ __forceinline__ void add_shfl(int off) {
+        ff o;
+        o.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+        o.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+        v = ff_add(v, o);
+    }
+    __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
+    __device__ __forceinline__ void merge(const Acc& o) { v = ff_add(v, o.v); }
+};
+
+// Reduce NQ accumulators over the block; thread 0 receives the totals in out[].
+// scratch: at least 32 * NQ doubles of shared memory.
+template <typename T, int NQ>
+__device__ __forceinline__ void block_sum(Acc<T> (&a)[NQ], double* scratch, double* out) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) a[q].add_shfl(off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) scratch[q * 32 + warp] = a[q].get();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += scratch[q * 32 + w];
+            out[q] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Max-reduction of a non-negative value over the block; thread 0 receives it.
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    double m = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) m = fmax(m, scratch[w]);
+    __syncthreads();
+    return m;
+}
+
+// Partial-sum bookkeeping of one reduction launch.
+struct RedSlot {
+    double* partials;    // [nq][gridDim.x]
+    double* result;      // [nq] finalised totals (max for quantities flagged in max_mask)
+    unsigned* ticket;    // zero between launches
+    int nq;
+    unsigned max_mask;   // bit q set: quantity q is a max, not a sum
+};
+
+// Called by every block after thread 0 holds its block totals in vals[0..nq).
+// The last block to arrive combines all partials in index order and resets the ticket.
+__device__ __forceinline__ void finalize_partials(const RedSlot& rs, const double* vals) {
+    __shared__ int am_last;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < rs.nq; ++q) rs.partials[q * gridDim.x + blockIdx.x] = vals[q];
+        __threadfence();
+        unsigned t = atomicAdd(rs.ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        for (int q = threadIdx.x >> 5; q < rs.nq; q += (blockDim.x >> 5) > 0 ? (blockDim.x >> 5) : 1) {
+            // one warp per quantity; fixed order within the warp: deterministic
+            const int lane = threadIdx.x & 31;
+            const bool is_max = (rs.max_mask >> q) & 1u;
+            double s = is_max ? 0.0 : 0.0;
+            for (unsigned b = lane; b < gridDim.x; b += 32) {
+                double x = ((volatile double*)rs.partials)[q * gridDim.x + b];
+                s = is_max ? fmax(s, x) : s + x;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                double o = __shfl_down_sync(0xffffffffu, s, off);
+                s = is_max ? fmax(s, o) : s + o;
+            }
+            if (lane == 0) rs.result[q] = s;
+        }
+        if (threadIdx.x == 0) *rs.ticket = 0u;
+    }
+}
+
+// Grid-wide barrier for cooperative launches with a bounded spin.
+// Returns false (and sets *err = 5, the timeout status) if the wait exceeded
+// `budget` SM clock cycles; callers then leave the kernel.
+struct GridBar {
+    unsigned* count;
+    volatile unsigned* gen;
+    int* err;
+    long long budget;
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBar& gb) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned my_gen = *gb.gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(gb.count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *gb.count = 0u;
+            __threadfence();
+            atomicAdd((unsigned*)gb.gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*gb.gen == my_gen) {
+                if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
+                    atomicCAS(gb.err, 0, 5);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+}  // namespace lbtr

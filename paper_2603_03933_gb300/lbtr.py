@@ -1,0 +1,295 @@
+"""Python binding of the C ABI in include/lbtr.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but
+check tensor properties, pass device pointers, sizes and the CUDA stream, and
+translate the returned status into an exception.  All arithmetic runs in the CUDA
+library liblbtr.so; there is no CPU fallback: if the library is missing or cannot
+be loaded, every call raises.
+
+Tensors: fields are contiguous CUDA tensors of N = M^d elements (any shape with that
+many elements, row-major with x fastest), float64 for LB_FP64 contexts and float32 for
+LB_MIXED contexts (lb_imex_tr_solve always takes float64).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+LB_FP64, LB_MIXED = 0, 1
+STATUS = {0: "LB_OK", 1: "LB_ERR_INVALID_ARG", 2: "LB_ERR_NOT_ZERO_MEAN", 3: "LB_ERR_NONFINITE",
+          4: "LB_ERR_NOCONV", 5: "LB_ERR_TIMEOUT", 6: "LB_ERR_CUDA", 7: "LB_ERR_OOM",
+          8: "LB_ERR_UNSUPPORTED"}
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblbtr.so")
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lb_problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("box", ctypes.c_double * 3),
+                ("xi", ctypes.c_double), ("tau", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
+class lb_sub_opts(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("eps_sub", ctypes.c_double), ("rel_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class lb_sub_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("dnorm", ctypes.c_double), ("model_value", ctypes.c_double),
+                ("newton_steps", ctypes.c_longlong)]
+
+
+class lb_eig_opts(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int), ("tol", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class lb_eig_info(ctypes.Structure):
+    _fields_ = [("lambda_min", ctypes.c_double), ("kappa_min", ctypes.c_double), ("residual", ctypes.c_double),
+                ("steps", ctypes.c_int), ("converged", ctypes.c_int)]
+
+
+class lb_tr_opts(ctypes.Structure):
+    _fields_ = [("gamma_c", ctypes.c_double), ("gamma_e", ctypes.c_double), ("gamma_lam", ctypes.c_double),
+                ("theta", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
+                ("mu0", ctypes.c_double), ("r0", ctypes.c_double), ("nu0", ctypes.c_double),
+                ("eps", ctypes.c_double), ("max_outer", ctypes.c_int), ("second_order", ctypes.c_int),
+                ("tol2", ctypes.c_double), ("sub", lb_sub_opts), ("eig", lb_eig_opts),
+                ("pcg_max_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double)]
+
+
+class lb_tr_info(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int), ("inner", ctypes.c_longlong), ("accepted", ctypes.c_int),
+                ("contracted", ctypes.c_int), ("shrunk", ctypes.c_int), ("energy", ctypes.c_double),
+                ("gmax", ctypes.c_double), ("lambda_min", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+# (name, restype, argtypes) of every exported entry point declared in include/lbtr.h
+_VP, _D, _DP = ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+SIGNATURES = [
+    ("lb_create", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("lb_destroy", ctypes.c_int, [_VP]),
+    ("lb_last_error", ctypes.c_char_p, [_VP]),
+    ("lb_workspace_bytes", ctypes.c_size_t, [_VP]),
+    ("lb_set_params", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lb_energy_grad", ctypes.c_int, [_VP, _VP, _DP, _VP, _DP, _VP]),
+    ("lb_hessvec", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    ("lb_default_sub_opts", None, [ctypes.POINTER(lb_sub_opts)]),
+    ("lb_tr_subproblem", ctypes.c_int, [_VP, _VP, _VP, _D, _VP, ctypes.POINTER(lb_sub_opts), _VP,
+                                        ctypes.POINTER(lb_sub_info), _VP]),
+    ("lb_default_eig_opts", None, [ctypes.POINTER(lb_eig_opts)]),
+    ("lb_lambda_min", ctypes.c_int, [_VP, _VP, ctypes.POINTER(lb_eig_opts), _VP,
+                                     ctypes.POINTER(lb_eig_info), _VP]),
+    ("lb_default_tr_opts", None, [ctypes.POINTER(lb_tr_opts)]),
+    ("lb_imex_tr_solve", ctypes.c_int, [_VP, _VP, ctypes.POINTER(lb_tr_opts), ctypes.POINTER(lb_tr_info), _VP]),
+    ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
+]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbtr.so (built in-tree by paper_2603_03933_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run `python -m paper_2603_03933_gb300.build`)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(ctx, status: int, where: str):
+    if status != 0:
+        msg = load().lb_last_error(ctx.handle if ctx is not None else None)
+        raise LBError(status, f"{where}: {msg.decode() if msg else ''}")
+
+
+@dataclass
+class Context:
+    """An lb_ctx* with the problem it was created for."""
+
+    handle: ctypes.c_void_p
+    dim: int
+    n: int
+    precision: int
+
+    @property
+    def npoints(self) -> int:
+        return self.n ** self.dim
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float64 if self.precision == LB_FP64 else torch.float32
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.lb_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _ptr(ctx: Context, t, name: str, dtype=None):
+    if t is None:
+        return None
+    torch = _torch()
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    want = dtype if dtype is not None else ctx.dtype
+    if t.dtype != want:
+        raise TypeError(f"{name} must be {want}, got {t.dtype}")
+    if t.numel() != ctx.npoints:
+        raise ValueError(f"{name} must have {ctx.npoints} elements, got {t.numel()}")
+    del torch
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lb_create(dim: int, n: int, box, xi: float, tau: float, gamma: float, precision: int = LB_FP64) -> Context:
+    """Create a context (C: lb_create).  box: lengths (L_x, L_y[, L_z])."""
+    lib = load()
+    box = list(box) + [1.0] * (3 - len(box))
+    prob = lb_problem(dim, n, (ctypes.c_double * 3)(*box[:3]), xi, tau, gamma)
+    h = ctypes.c_void_p()
+    st = lib.lb_create(ctypes.byref(prob), precision, ctypes.byref(h))
+    if st != 0:
+        raise LBError(st, "lb_create")
+    return Context(h, dim, n, precision)
+
+
+def lb_create_from_array_box(shape, box_per_axis, xi, tau, gamma, precision=LB_FP64) -> Context:
+    """Create from a numpy-style shape ([y][x] or [z][y][x]) and box lengths in array axis order."""
+    dim = len(shape)
+    if len(set(shape)) != 1:
+        raise ValueError("grids must have the same number of points on every axis")
+    box_xyz = list(box_per_axis)[::-1]
+    return lb_create(dim, int(shape[0]), box_xyz, xi, tau, gamma, precision)
+
+
+def lb_destroy(ctx: Context):
+    if ctx.handle:
+        load().lb_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def lb_set_params(ctx: Context, xi: float, tau: float, gamma: float):
+    _check(ctx, load().lb_set_params(ctx.handle, xi, tau, gamma), "lb_set_params")
+
+
+def lb_workspace_bytes(ctx: Context) -> int:
+    return int(load().lb_workspace_bytes(ctx.handle))
+
+
+def lb_energy_grad(ctx: Context, phi, grad=None, stream=None):
+    """(E, max|g|) with g written into `grad` when given (C: lb_energy_grad)."""
+    e = ctypes.c_double()
+    gm = ctypes.c_double(float("nan"))
+    st = load().lb_energy_grad(ctx.handle, _ptr(ctx, phi, "phi"), ctypes.byref(e), _ptr(ctx, grad, "grad"),
+                               ctypes.byref(gm) if grad is not None else None, _stream(stream))
+    _check(ctx, st, "lb_energy_grad")
+    return e.value, (gm.value if grad is not None else None)
+
+
+def lb_hessvec(ctx: Context, phi, v, hv, stream=None):
+    """hv = H v (C: lb_hessvec); asynchronous on the stream."""
+    st = load().lb_hessvec(ctx.handle, _ptr(ctx, phi, "phi"), _ptr(ctx, v, "v"), _ptr(ctx, hv, "hv"),
+                           _stream(stream))
+    _check(ctx, st, "lb_hessvec")
+    return hv
+
+
+def default_sub_opts() -> lb_sub_opts:
+    o = lb_sub_opts()
+    load().lb_default_sub_opts(ctypes.byref(o))
+    return o
+
+
+def lb_tr_subproblem(ctx: Context, phi, g, r: float, d, d0=None, opts: lb_sub_opts | None = None,
+                     stream=None, raise_on_noconv: bool = True) -> dict:
+    """Algorithm 3 (C: lb_tr_subproblem); returns the info struct as a dict."""
+    o = opts if opts is not None else default_sub_opts()
+    info = lb_sub_info()
+    st = load().lb_tr_subproblem(ctx.handle, _ptr(ctx, phi, "phi"), _ptr(ctx, g, "g"), float(r),
+                                 _ptr(ctx, d0, "d0"), ctypes.byref(o), _ptr(ctx, d, "d"), ctypes.byref(info),
+                                 _stream(stream))
+    if not (st == 4 and not raise_on_noconv):
+        _check(ctx, st, "lb_tr_subproblem")
+    return {"iterations": info.iterations, "converged": bool(info.converged), "residual": info.residual,
+            "lambda": info.lambda_, "dnorm": info.dnorm, "model_value": info.model_value,
+            "newton_steps": info.newton_steps, "status": st}
+
+
+def default_eig_opts() -> lb_eig_opts:
+    o = lb_eig_opts()
+    load().lb_default_eig_opts(ctypes.byref(o))
+    return o
+
+
+def lb_lambda_min(ctx: Context, phi, vec=None, opts: lb_eig_opts | None = None, stream=None,
+                  raise_on_noconv: bool = True) -> dict:
+    """Smallest Hessian eigenvalue estimate (C: lb_lambda_min)."""
+    o = opts if opts is not None else default_eig_opts()
+    info = lb_eig_info()
+    st = load().lb_lambda_min(ctx.handle, _ptr(ctx, phi, "phi"), ctypes.byref(o), _ptr(ctx, vec, "vec"),
+                              ctypes.byref(info), _stream(stream))
+    if not (st == 4 and not raise_on_noconv):
+        _check(ctx, st, "lb_lambda_min")
+    return {"lambda_min": info.lambda_min, "kappa_min": info.kappa_min, "residual": info.residual,
+            "steps": info.steps, "converged": bool(info.converged), "status": st}
+
+
+def default_tr_opts() -> lb_tr_opts:
+    o = lb_tr_opts()
+    load().lb_default_tr_opts(ctypes.byref(o))
+    return o
+
+
+def lb_imex_tr_solve(ctx: Context, phi64, opts: lb_tr_opts | None = None, stream=None,
+                     raise_on_noconv: bool = True) -> dict:
+    """IMEX-TR (C: lb_imex_tr_solve); phi64 (float64 CUDA tensor) is updated in place."""
+    torch = _torch()
+    o = opts if opts is not None else default_tr_opts()
+    info = lb_tr_info()
+    st = load().lb_imex_tr_solve(ctx.handle, _ptr(ctx, phi64, "phi", torch.float64), ctypes.byref(o),
+                                 ctypes.byref(info), _stream(stream))
+    if not (st == 4 and not raise_on_noconv):
+        _check(ctx, st, "lb_imex_tr_solve")
+    return {"outer": info.outer, "inner": info.inner, "accepted": info.accepted, "contracted": info.contracted,
+            "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
+            "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": st}
+
+
+def lb_set_barrier_budget(ctx: Context, cycles: int):
+    _check(ctx, load().lb_set_barrier_budget(ctx.handle, int(cycles)), "lb_set_barrier_budget")
