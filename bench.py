@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the LB IMEX-TR hot path on GB300 (one JSON line on stdout).
+
+Workload: 3D LB at scale, 128^3 grid, cubic box side 4*pi*sqrt(2), tau = -0.05,
+gamma = 0.3, phi0 ~ N(0, 0.05^2) mean-removed (seeded), mixed precision (float FFTs,
+diagonals and pointwise updates; double reductions).
+
+A step is a batch of `--batch` Hessian-vector products H v = P[F^{-1} Lambda F v +
+F''(phi) v] over a rotating pool of distinct (phi, v, Hv) triples whose total size is
+three times the 129 MB L2, so every product reads its inputs from HBM.  `value` is
+products per second over the timed steps with inputs resident in HBM; `e2e` is the same
+metric through the C ABI with the inputs copied from pinned host memory and the results
+copied back inside the timed region.  The FP64 path and 256^3 are reported beside it.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian-vector products/s & TR iters/s at 128³, mixed vs FP64 GPU; HBM GB/s"
+UNIT = "HVP/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# ncu DRAM traffic per launch of a kernel class, with the hash of the CUDA sources it
+# was captured from (a traffic figure is reported only while the sources match).
+TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2603_03933_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.idx = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_hvp_rate(M: int, seconds: float = 12.0) -> dict:
+    """The FP64 CPU oracle's Hessian-vector products on the same workload (bounded sample)."""
+    import numpy as np
+    from oracle import lb as olb
+    from paper_2603_03933_gb300 import inputs
+    w = inputs.config_3d_scale(M)
+    p = olb.Problem.from_workload(w)
+    rng = np.random.default_rng(77)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        v = inputs.remove_mean(rng.standard_normal(w.shape))
+        olb.hessvec(p, w.phi0, v)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= 50:
+            break
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} FP64 oracle Hessian-vector products at {M}^3 ({el:.1f} s, numpy, 1 thread)"}
+
+
+def run_reference(args, rank: int):
+    """The oracle as it stands: each step is one FP64 Hessian-vector product at --size."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import lb as olb
+    from paper_2603_03933_gb300 import inputs
+    w = inputs.config_3d_scale(args.size)
+    p = olb.Problem.from_workload(w)
+    vs = [inputs.gaussian_field(w.shape, 1.0, 2000 + i) for i in range(2)]
+    for i in range(args.warmup):
+        olb.hessvec(p, w.phi0, vs[i % 2])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        olb.hessvec(p, w.phi0, vs[i % 2])
+    total = time.perf_counter() - t0
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"3D LB at scale {args.size}^3 (tau -0.05, gamma 0.3, box 4*pi*sqrt(2))",
+                       "step": "1 Hessian-vector product of the FP64 CPU oracle", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle Hessian-vector products at {args.size}^3 "
+                                       "(numpy, 1 thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def hvp_pool(lbtr, ctx, w, M, dtype, count, device):
+    import torch
+    from paper_2603_03933_gb300 import inputs
+    pool = []
+    for i in range(count):
+        phi = torch.tensor(w.phi0 if i == 0 else inputs.gaussian_field(w.shape, 0.05, 1000 + i),
+                           dtype=dtype, device=device)
+        v = torch.tensor(inputs.gaussian_field(w.shape, 1.0, 2000 + i), dtype=dtype, device=device)
+        pool.append((phi, v, torch.empty_like(v)))
+    return pool
+
+
+def time_hvp(lbtr, ctx, pool, batch, steps, warmup, world):
+    """Per-step device time (s) of `batch` products cycling through the pool."""
+    import torch
+    s = torch.cuda.current_stream()
+    k = 0
+
+    def step():
+        nonlocal k
+        for _ in range(batch):
+            phi, v, hv = pool[k % len(pool)]
+            lbtr.lb_hessvec(ctx, phi, v, hv, stream=s)
+            k += 1
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lbtr", choices=["lbtr", "reference"])
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only-hvp", action="store_true",
+                    help="time only the mixed HVP at --size (small runs for profilers)")
+    ap.add_argument("--pool", type=int, default=0, help="override the number of (phi, v, Hv) triples")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_2603_03933_gb300 import inputs, lbtr
+    lbtr.load()
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    M = args.size
+    w = inputs.config_3d_scale(M)
+    field_bytes = 4 * w.n_points
+    npool = args.pool if args.pool > 0 else max(4, math.ceil(3 * L2_BYTES / (3 * field_bytes)))
+
+    ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, lbtr.LB_MIXED)
+    pool = hvp_pool(lbtr, ctx, w, M, torch.float32, npool, dev)
+
+    # ---- timed region: value --------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    dt = time_hvp(lbtr, ctx, pool, args.batch, args.steps, args.warmup, world)
+    clk = clocks.stop()
+    dt = max_over_ranks(dt, world)
+    hvps = args.batch * args.steps * world
+    value = hvps / dt
+
+    if args.only_hvp:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "mode": "only-hvp",
+                              "size": M, "pool": npool, "us_per_hvp": dt / (args.batch * args.steps * world) * 1e6}),
+                  flush=True)
+        return
+
+    # ---- per-kernel live timing (CUDA events on the launching stream) -----------
+    lbtr.lb_profile_enable(ctx, True)
+    time_hvp(lbtr, ctx, pool, args.batch, max(3, args.steps // 4), 1, 1)
+    prof = lbtr.lb_profile_read(ctx)
+    lbtr.lb_profile_enable(ctx, False)
+    peaks = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, nl, by = prof[dom]
+    achieved = (by / nl) / (ms / nl / 1e3) / 1e9
+    tr = TRAFFIC.get(dom)
+    traffic = tr[0] if (tr and tr[1] == csrc_hash()) else None
+    hvp_time = dt / (args.batch * args.steps)
+    hvp_alg = 3 * field_bytes
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": peaks["source"],
+                "hvp": {"alg_bytes": hvp_alg, "us": hvp_time * 1e6,
+                        "achieved_gbs": hvp_alg / hvp_time / 1e9,
+                        "frac": hvp_alg / hvp_time / 1e9 / peaks["hbm_gbs"]},
+                "per_kernel": {k: {"launches": v[1], "avg_us": 1e3 * v[0] / v[1],
+                                   "alg_gbs": (v[2] / v[1]) / (v[0] / v[1] / 1e3) / 1e9,
+                                   "share": v[0] / sum(x[0] for x in prof.values())}
+                               for k, v in prof.items() if v[1] > 0}}
+
+    # ---- FP64 path at the same size -------------------------------------------
+    ctx64 = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, lbtr.LB_FP64)
+    pool64 = [(a.double(), b.double(), c.double()) for a, b, c in pool[: max(2, npool // 2)]]
+    dt64 = time_hvp(lbtr, ctx64, pool64, 4, 3, 1, 1)
+    fp64 = {"value": 12 / dt64, "unit": UNIT, "us_per_hvp": dt64 / 12 * 1e6}
+    del pool64, ctx64
+
+    # ---- e2e: host buffers, copies inside the timed region ----------------------
+    s = torch.cuda.current_stream()
+    nb = args.batch
+    phi_h = pool[0][0].cpu().pin_memory()
+    v_h = [pool[i % npool][1].cpu().pin_memory() for i in range(nb)]
+    out_h = [torch.empty(w.shape, dtype=torch.float32).pin_memory() for _ in range(nb)]
+    phi_d = torch.empty_like(pool[0][0])
+    v_d = [torch.empty_like(pool[0][1]) for _ in range(2)]
+    hv_d = [torch.empty_like(pool[0][1]) for _ in range(2)]
+
+    def e2e_step():
+        phi_d.copy_(phi_h, non_blocking=True)
+        for i in range(nb):
+            v_d[i % 2].copy_(v_h[i], non_blocking=True)
+            lbtr.lb_hessvec(ctx, phi_d, v_d[i % 2], hv_d[i % 2], stream=s)
+            out_h[i].copy_(hv_d[i % 2], non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    dte = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world)
+    e2e = {"value": nb * e2e_steps * world / dte, "unit": UNIT,
+           "h2d_bytes_per_step": (1 + nb) * field_bytes, "d2h_bytes_per_step": nb * field_bytes}
+
+    # ---- 256^3 at the same settings (context, not the headline) ------------------
+    big = None
+    if M == 128 and world == 1:
+        try:
+            w2 = inputs.config_3d_scale(256)
+            ctx2 = lbtr.lb_create_from_array_box(w2.shape, w2.box, w2.xi, w2.tau, w2.gamma, lbtr.LB_MIXED)
+            pool2 = []
+            for i in range(4):
+                pool2.append((torch.tensor(w2.phi0, dtype=torch.float32, device=dev),
+                              torch.tensor(inputs.gaussian_field(w2.shape, 1.0, 3000 + i), dtype=torch.float32,
+                                           device=dev),
+                              torch.empty(w2.shape, dtype=torch.float32, device=dev)))
+            d2 = time_hvp(lbtr, ctx2, pool2, 8, 4, 1, 1)
+            big = {"value": 32 / d2, "unit": UNIT, "us_per_hvp": d2 / 32 * 1e6,
+                   "alg_gbs": 3 * 4 * w2.n_points / (d2 / 32) / 1e9}
+            del pool2, ctx2
+        except Exception as ex:  # report, do not hide
+            big = {"error": str(ex)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_hvp_rate(M)
+
+    launches_per_hvp = 5
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": f"3D LB at scale {M}^3, mixed precision (tau -0.05, gamma 0.3, "
+                               f"box 4*pi*sqrt(2), phi0 ~ N(0, 0.05^2))",
+                   "step": f"{args.batch} Hessian-vector products", "pool_triples": npool,
+                   "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": launches_per_hvp * args.batch * args.steps,
+        "fp64": fp64, "size_256": big,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -214,6 +214,29 @@ void lb_default_tr_opts(lb_tr_opts *o);
 lb_status lb_imex_tr_solve(lb_ctx *ctx, double *phi_inout, const lb_tr_opts *opts,
                            lb_tr_info *info, lb_stream stream);
 
+/* Profiling aid.  Kernel classes of the library's launches: */
+typedef enum {
+    LB_K_XFWD = 0,     /* forward x-row real transform with its pointwise preprocessing */
+    LB_K_XINV = 1,     /* inverse x-row real transform with its pointwise postprocessing */
+    LB_K_XMID = 2,     /* fused inverse -> pointwise -> forward x-row transform */
+    LB_K_COLY = 3,     /* column transform along y (non-innermost in 3D) */
+    LB_K_COLI = 4,     /* innermost column transform with the reciprocal-space diagonal */
+    LB_K_SECULAR = 5,  /* cooperative secular-equation Newton solve */
+    LB_K_REDUCE = 6,   /* physical-space reductions and elementwise kernels */
+    LB_K_COUNT = 7
+} lb_kernel_class;
+
+/* enable != 0: from now on every kernel the context launches is bracketed by CUDA
+ * events on its stream, and the totals below are reset; enable == 0 stops that. */
+lb_status lb_profile_enable(lb_ctx *ctx, int enable);
+
+/* Synchronise the recorded events and return, for kernel class `kclass`, the summed
+ * device time in ms, the number of launches and the summed algorithmic bytes (the
+ * arrays each launch must read and write once: inputs, outputs and the spectra it
+ * transforms, counted at the context's working precision). */
+lb_status lb_profile_read(lb_ctx *ctx, int kclass, double *total_ms, long long *launches,
+                          double *alg_bytes);
+
 /* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
  * (0 restores the default of about two seconds).  Lets tests exercise the
  * LB_ERR_TIMEOUT path without a hang. */

@@ -117,6 +117,24 @@ lb_status lb_set_params(lb_ctx* ctx, double xi, double tau, double gamma) {
     return LB_OK;
 }
 
+lb_status lb_profile_enable(lb_ctx* ctx, int enable) {
+    if (!ctx) return LB_ERR_INVALID_ARG;
+    ctx->prof.reset();
+    lbtr::Prof* p = enable ? &ctx->prof : nullptr;
+    if (ctx->p64) ctx->p64->set_prof(p);
+    if (ctx->p32) ctx->p32->set_prof(p);
+    return LB_OK;
+}
+
+lb_status lb_profile_read(lb_ctx* ctx, int kclass, double* total_ms, long long* launches, double* alg_bytes) {
+    if (!ctx || kclass < 0 || kclass >= LB_K_COUNT) return LB_ERR_INVALID_ARG;
+    ctx->prof.flush();
+    if (total_ms) *total_ms = ctx->prof.ms(kclass);
+    if (launches) *launches = ctx->prof.launches(kclass);
+    if (alg_bytes) *alg_bytes = ctx->prof.bytes(kclass);
+    return LB_OK;
+}
+
 lb_status lb_set_barrier_budget(lb_ctx* ctx, long long cycles) {
     if (!ctx) return LB_ERR_INVALID_ARG;
     if (ctx->p64) ctx->p64->set_barrier_budget(cycles);

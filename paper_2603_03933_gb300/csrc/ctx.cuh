@@ -23,6 +23,7 @@ struct lb_ctx {
     double* d_scal = nullptr;            // small device scalars
     void* tmp_w[2] = {nullptr, nullptr}; // two working-type fields
     double* f64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // FP64 fields of the outer loop
+    lbtr::Prof prof;                     // per-kernel-class event timing (profiling aid)
 
     ~lb_ctx() {
         delete p64;

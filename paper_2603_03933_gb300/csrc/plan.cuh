@@ -6,6 +6,7 @@
 
 #include "aux_kernels.cuh"
 #include "passes.cuh"
+#include "prof.cuh"
 
 namespace lbtr {
 
@@ -71,6 +72,7 @@ public:
     // first error returned by a cooperative launch since the last call (then cleared)
     cudaError_t take_launch_error() { cudaError_t e = launch_err_; launch_err_ = cudaSuccess; return e; }
     void reset_barrier(cudaStream_t s);
+    void set_prof(Prof* p) { prof_ = p; }
 
     // accessors
     const double* slot(int k) const { return d_result_ + k * SLOT_Q; }
@@ -128,6 +130,9 @@ private:
     ImexState* d_state_ = nullptr;
     int max_blocks_ = 0;
     cudaError_t launch_err_ = cudaSuccess;
+    Prof* prof_ = nullptr;
+    double fb() const { return (double)n_ * sizeof(T); }
+    double sb() const { return (double)spec_len() * sizeof(C); }
 };
 
 }  // namespace lbtr

@@ -181,12 +181,17 @@ void Plan<T>::xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0,
     a.red = redslot(slot, mode == XF_ENERGY ? 4 : 1, 0u);
     a.done = done;
     int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     LB_SWITCH_M(m_, {
         if (mode == XF_PLAIN) launch_xfwd<T, M, XF_PLAIN>(a, grid, s);
         else if (mode == XF_HVPMEAN) launch_xfwd<T, M, XF_HVPMEAN>(a, grid, s);
         else if (mode == XF_ENERGY) launch_xfwd<T, M, XF_ENERGY>(a, grid, s);
         else launch_xfwd<T, M, XF_IMEX0>(a, grid, s);
     });
+    if (prof_) {
+        double nf = mode == XF_HVPMEAN ? 2 : mode == XF_IMEX0 ? (d0 ? 3 : 2) : 1;
+        prof_->end(K_XFWD, e0, s, nf * fb() + sb());
+    }
 }
 
 template <typename T>
@@ -199,11 +204,13 @@ void Plan<T>::xinv(int mode, const C* spec, T* out, const T* phi, const T* v, co
     a.red = redslot(slot, 1, 1u);
     a.done = done;
     int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     LB_SWITCH_M(m_, {
         if (mode == XI_PLAIN) launch_xinv<T, M, XI_PLAIN>(a, grid, s);
         else if (mode == XI_HVP) launch_xinv<T, M, XI_HVP>(a, grid, s);
         else launch_xinv<T, M, XI_GRAD>(a, grid, s);
     });
+    if (prof_) prof_->end(K_XINV, e0, s, sb() + (mode == XI_HVP ? 3 : mode == XI_GRAD ? 2 : 1) * fb());
 }
 
 template <typename T>
@@ -214,10 +221,12 @@ void Plan<T>::xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStr
     a.model = model_; a.model.eta = (T)eta;
     a.done = done;
     int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     LB_SWITCH_M(m_, {
         if (mode == XM_IMEX) launch_xmid<T, M, XM_IMEX>(a, grid, s);
         else launch_xmid<T, M, XM_TOP>(a, grid, s);
     });
+    if (prof_) prof_->end(K_XMID, e0, s, 2 * sb() + (mode == XM_IMEX ? 2 : 1) * fb());
 }
 
 // axis: 1 = Y, 2 = Z
@@ -248,6 +257,7 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     a.sigma = (T)sigma; a.lam = lam;
     a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : 1, 0u);
     a.done = done;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     LB_SWITCH_M(m_, {
         switch (mode) {
             case C_FWD: launch_cols<T, M, C_FWD>(a, grid, s); break;
@@ -261,6 +271,11 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
             default: launch_cols<T, M, C_MSCALE_IN>(a, grid, s); break;
         }
     });
+    if (prof_) {
+        const bool innermost = (dim_ == 3) ? axis == 2 : axis == 1;
+        double ns = mode == C_QUAD_E ? 1 : (mode == C_IMEX_OUT || mode == C_TOP_OUT) ? 3 : 2;
+        prof_->end(innermost ? K_COLI : K_COLY, e0, s, ns * sb());
+    }
 }
 
 template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cudaStream_t s) {
@@ -299,6 +314,7 @@ template <typename T> void Plan<T>::phys_reduce(int op, const T* x, const T* y, 
     a.x = x; a.y = y; a.n = n_;
     int grid = (int)std::min<long long>(max_blocks_, (n_ + 255) / 256);
     if (grid < 1) grid = 1;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     if (op == R_DOT) {
         a.red = redslot(slot, 1, 0u);
         k_physred<T, R_DOT><<<grid, 256, 0, s>>>(a);
@@ -309,6 +325,7 @@ template <typename T> void Plan<T>::phys_reduce(int op, const T* x, const T* y, 
         a.red = redslot(slot, 2, 0u);
         k_physred<T, R_SUM_SUMSQ><<<grid, 256, 0, s>>>(a);
     }
+    if (prof_) prof_->end(K_REDUCE, e0, s, (op == R_DOT ? 2 : 1) * fb());
 }
 
 template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaStream_t s) {
@@ -326,9 +343,11 @@ template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaSt
     a.check = check; a.max_iter = max_iter_;
     a.xi2 = (T)xi2_;
     void* args[] = {&a};
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_secular<T>, dim3(coop_blocks_), dim3(256), args,
                                                 3 * m_ * sizeof(T), s);
     if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+    if (prof_) prof_->end(K_SECULAR, e0, s, sb());
 }
 
 template <typename T>

@@ -89,8 +89,11 @@ SIGNATURES = [
                                      ctypes.POINTER(lb_eig_info), _VP]),
     ("lb_default_tr_opts", None, [ctypes.POINTER(lb_tr_opts)]),
     ("lb_imex_tr_solve", ctypes.c_int, [_VP, _VP, ctypes.POINTER(lb_tr_opts), ctypes.POINTER(lb_tr_info), _VP]),
+    ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
 ]
+KERNEL_CLASSES = ["xfwd", "xinv", "xmid", "col_y", "col_inner", "secular", "reduce"]
 
 _lib = None
 
@@ -293,3 +296,19 @@ def lb_imex_tr_solve(ctx: Context, phi64, opts: lb_tr_opts | None = None, stream
 
 def lb_set_barrier_budget(ctx: Context, cycles: int):
     _check(ctx, load().lb_set_barrier_budget(ctx.handle, int(cycles)), "lb_set_barrier_budget")
+
+
+def lb_profile_enable(ctx: Context, enable: bool = True):
+    """Start (and reset) or stop per-kernel-class event timing (C: lb_profile_enable)."""
+    _check(ctx, load().lb_profile_enable(ctx.handle, 1 if enable else 0), "lb_profile_enable")
+
+
+def lb_profile_read(ctx: Context) -> dict:
+    """{class: (total_ms, launches, algorithmic_bytes)} for every kernel class (C: lb_profile_read)."""
+    out = {}
+    for k, name in enumerate(KERNEL_CLASSES):
+        ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        _check(ctx, load().lb_profile_read(ctx.handle, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
+               "lb_profile_read")
+        out[name] = (ms.value, n.value, b.value)
+    return out
