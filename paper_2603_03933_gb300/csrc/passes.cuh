@@ -80,6 +80,7 @@ template <typename T> struct XfArgs {
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(x_nt(M)) k_xfwd(XfArgs<T> a) {
     constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    constexpr int IT = H * NL / NT;          // complex pairs per thread (8)
     using C = cplx<T>;
     if (a.done && *(volatile const int*)a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -87,49 +88,65 @@ __global__ void __launch_bounds__(x_nt(M)) k_xfwd(XfArgs<T> a) {
     C* buf = tw + M;
     C* nyqs = buf + H * LD;
     double* red = reinterpret_cast<double*>(nyqs + NL);
+    const int row0 = blockIdx.x * NL;
+    const C zero = mk<T>((T)0, (T)0);
+
+    // issue every global load of this thread before using any of them
+    C z[IT], p[IT], gg[IT];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int n = w % H, row = row0 + w / H;
+        const bool ok = row < a.rows;
+        const size_t idx = (size_t)row * H + n;
+        if (MODE == XF_IMEX0) {
+            p[t] = ok ? reinterpret_cast<const C*>(a.phi)[idx] : zero;
+            gg[t] = ok ? reinterpret_cast<const C*>(a.g)[idx] : zero;
+            z[t] = (ok && a.d0) ? reinterpret_cast<const C*>(a.d0)[idx] : zero;
+        } else {
+            z[t] = ok ? reinterpret_cast<const C*>(a.in)[idx] : zero;
+            if (MODE == XF_HVPMEAN) p[t] = ok ? reinterpret_cast<const C*>(a.phi)[idx] : zero;
+        }
+    }
     for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
 
-    const int row0 = blockIdx.x * NL;
     constexpr int NQ = (MODE == XF_ENERGY) ? 4 : 1;
     Acc<T> acc[NQ];
     T ds = (T)0;
     if (MODE == XF_IMEX0 && a.d0 == nullptr) ds = (T)(*a.dscale);
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int n = w % H, l = w / H;
-        int row = row0 + l;
-        C z = mk<T>((T)0, (T)0);
-        if (row < a.rows) {
-            size_t idx = (size_t)row * H + n;
-            if (MODE == XF_IMEX0) {
-                C p = reinterpret_cast<const C*>(a.phi)[idx];
-                C gg = reinterpret_cast<const C*>(a.g)[idx];
-                C d = a.d0 ? reinterpret_cast<const C*>(a.d0)[idx] : mk<T>(ds * gg.x, ds * gg.y);
-                z.x = d.x - a.model.eta * (gg.x + f2v(a.model, p.x) * d.x);
-                z.y = d.y - a.model.eta * (gg.y + f2v(a.model, p.y) * d.y);
-            } else {
-                z = reinterpret_cast<const C*>(a.in)[idx];
-                if (MODE == XF_HVPMEAN) {
-                    C p = reinterpret_cast<const C*>(a.phi)[idx];
-                    acc[0].add(f2v(a.model, p.x) * z.x);
-                    acc[0].add(f2v(a.model, p.y) * z.y);
-                } else if (MODE == XF_ENERGY) {
-                    acc[0].add(f0v(a.model, z.x));
-                    acc[0].add(f0v(a.model, z.y));
-                    acc[NQ > 1 ? 1 : 0].add(f1v(a.model, z.x));
-                    acc[NQ > 1 ? 1 : 0].add(f1v(a.model, z.y));
-                    acc[NQ > 2 ? 2 : 0].add(z.x + z.y);
-                    acc[NQ > 3 ? 3 : 0].add(z.x * z.x + z.y * z.y);
-                }
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int n = w % H, l = w / H;
+        C v = z[t];
+        if (MODE == XF_IMEX0) {
+            C d = a.d0 ? v : mk<T>(ds * gg[t].x, ds * gg[t].y);
+            v.x = d.x - a.model.eta * (gg[t].x + f2v(a.model, p[t].x) * d.x);
+            v.y = d.y - a.model.eta * (gg[t].y + f2v(a.model, p[t].y) * d.y);
+            if (row0 + l >= a.rows) v = zero;
+        } else if (MODE == XF_HVPMEAN) {
+            acc[0].add(f2v(a.model, p[t].x) * v.x);
+            acc[0].add(f2v(a.model, p[t].y) * v.y);
+        } else if (MODE == XF_ENERGY) {
+            if (row0 + l < a.rows) {
+                acc[0].add(f0v(a.model, v.x));
+                acc[0].add(f0v(a.model, v.y));
+                acc[NQ > 1 ? 1 : 0].add(f1v(a.model, v.x));
+                acc[NQ > 1 ? 1 : 0].add(f1v(a.model, v.y));
+                acc[NQ > 2 ? 2 : 0].add(v.x + v.y);
+                acc[NQ > 3 ? 3 : 0].add(v.x * v.x + v.y * v.y);
             }
         }
-        buf[n * LD + l] = z;
+        buf[n * LD + l] = v;
     }
     __syncthreads();
     fft_lines<T, -1, H, NL, NT>(buf, tw, M);
     r2c_post<T, H, NL, NT>(buf, nyqs, tw, M);
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int k = w % H, l = w / H;
-        int row = row0 + l;
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int k = w % H, l = w / H;
+        const int row = row0 + l;
         if (row < a.rows) a.main[(size_t)row * H + k] = buf[k * LD + l];
     }
     for (int l = threadIdx.x; l < NL; l += NT)
@@ -169,6 +186,7 @@ template <typename T> struct XiArgs {
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(x_nt(M)) k_xinv(XiArgs<T> a) {
     constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    constexpr int IT = H * NL / NT;
     using C = cplx<T>;
     if (a.done && *(volatile const int*)a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -176,42 +194,52 @@ __global__ void __launch_bounds__(x_nt(M)) k_xinv(XiArgs<T> a) {
     C* buf = tw + M;
     C* nyqs = buf + H * LD;
     double* red = reinterpret_cast<double*>(nyqs + NL);
-    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
     const int row0 = blockIdx.x * NL;
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int k = w % H, l = w / H;
-        int row = row0 + l;
-        buf[k * LD + l] = row < a.rows ? a.main[(size_t)row * H + k] : mk<T>((T)0, (T)0);
+    const C zero = mk<T>((T)0, (T)0);
+    // spectrum rows, and the physical fields of the epilogue, all requested up front
+    C sp[IT], p[IT], vv[IT];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int k = w % H, row = row0 + w / H;
+        const bool ok = row < a.rows;
+        const size_t idx = (size_t)row * H + k;
+        sp[t] = ok ? a.main[idx] : zero;
+        if (MODE != XI_PLAIN) p[t] = ok ? reinterpret_cast<const C*>(a.phi)[idx] : zero;
+        if (MODE == XI_HVP) vv[t] = ok ? reinterpret_cast<const C*>(a.v)[idx] : zero;
     }
     for (int l = threadIdx.x; l < NL; l += NT)
-        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : mk<T>((T)0, (T)0);
+        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : zero;
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    T mean = (T)0;
+    if (MODE != XI_PLAIN) mean = (T)(*a.msum * a.inv_n);
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        buf[(w % H) * LD + w / H] = sp[t];
+    }
     __syncthreads();
     c2r_pre<T, H, NL, NT>(buf, nyqs, tw, M);
     fft_lines<T, +1, H, NL, NT>(buf, tw, M);
-    T mean = (T)0;
-    if (MODE != XI_PLAIN) mean = (T)(*a.msum * a.inv_n);
     double mx = 0.0;
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int n = w % H, l = w / H;
-        int row = row0 + l;
-        if (row >= a.rows) continue;
-        size_t idx = (size_t)row * H + n;
-        C z = buf[n * LD + l];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int n = w % H, l = w / H;
+        const int row = row0 + l;
+        C zz = buf[n * LD + l];
         C o;
         if (MODE == XI_PLAIN) {
-            o = mk<T>(z.x * a.oscale, z.y * a.oscale);
+            o = mk<T>(zz.x * a.oscale, zz.y * a.oscale);
         } else if (MODE == XI_HVP) {
-            C p = reinterpret_cast<const C*>(a.phi)[idx];
-            C vv = reinterpret_cast<const C*>(a.v)[idx];
-            o.x = z.x + f2v(a.model, p.x) * vv.x - mean;
-            o.y = z.y + f2v(a.model, p.y) * vv.y - mean;
+            o.x = zz.x + f2v(a.model, p[t].x) * vv[t].x - mean;
+            o.y = zz.y + f2v(a.model, p[t].y) * vv[t].y - mean;
         } else {
-            C p = reinterpret_cast<const C*>(a.phi)[idx];
-            o.x = z.x + f1v(a.model, p.x) - mean;
-            o.y = z.y + f1v(a.model, p.y) - mean;
-            mx = fmax(mx, fmax(fabs((double)o.x), fabs((double)o.y)));
+            o.x = zz.x + f1v(a.model, p[t].x) - mean;
+            o.y = zz.y + f1v(a.model, p[t].y) - mean;
+            if (row < a.rows) mx = fmax(mx, fmax(fabs((double)o.x), fabs((double)o.y)));
         }
-        reinterpret_cast<C*>(a.out)[idx] = o;
+        if (row < a.rows) reinterpret_cast<C*>(a.out)[(size_t)row * H + n] = o;
     }
     if (MODE == XI_GRAD) {
         double m = block_max(mx, red);
@@ -242,40 +270,51 @@ template <typename T> struct XmArgs {
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(x_nt(M)) k_xmid(XmArgs<T> a) {
     constexpr int H = M / 2, NL = x_nl(M), NT = x_nt(M), LD = NL + 1;
+    constexpr int IT = H * NL / NT;
     using C = cplx<T>;
     if (a.done && *(volatile const int*)a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + M;
     C* nyqs = buf + H * LD;
-    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
     const int row0 = blockIdx.x * NL;
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int k = w % H, l = w / H;
-        int row = row0 + l;
-        buf[k * LD + l] = row < a.rows ? a.main[(size_t)row * H + k] : mk<T>((T)0, (T)0);
+    const C zero = mk<T>((T)0, (T)0);
+    C sp[IT], p[IT], gg[IT];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int k = w % H, row = row0 + w / H;
+        const bool ok = row < a.rows;
+        const size_t idx = (size_t)row * H + k;
+        sp[t] = ok ? a.main[idx] : zero;
+        p[t] = ok ? reinterpret_cast<const C*>(a.phi)[idx] : zero;
+        if (MODE == XM_IMEX) gg[t] = ok ? reinterpret_cast<const C*>(a.g)[idx] : zero;
     }
     for (int l = threadIdx.x; l < NL; l += NT)
-        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : mk<T>((T)0, (T)0);
+        nyqs[l] = (row0 + l < a.rows) ? a.nyq[row0 + l] : zero;
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        buf[(w % H) * LD + w / H] = sp[t];
+    }
     __syncthreads();
     c2r_pre<T, H, NL, NT>(buf, nyqs, tw, M);
     fft_lines<T, +1, H, NL, NT>(buf, tw, M);
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int n = w % H, l = w / H;
-        int row = row0 + l;
-        C z = buf[n * LD + l];
-        C o = mk<T>((T)0, (T)0);
-        if (row < a.rows) {
-            size_t idx = (size_t)row * H + n;
-            C p = reinterpret_cast<const C*>(a.phi)[idx];
-            T dx = z.x * a.scale, dy = z.y * a.scale;
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int n = w % H, l = w / H;
+        C zz = buf[n * LD + l];
+        C o = zero;
+        if (row0 + l < a.rows) {
+            T dx = zz.x * a.scale, dy = zz.y * a.scale;
             if (MODE == XM_IMEX) {
-                C gg = reinterpret_cast<const C*>(a.g)[idx];
-                o.x = dx - a.model.eta * (gg.x + f2v(a.model, p.x) * dx);
-                o.y = dy - a.model.eta * (gg.y + f2v(a.model, p.y) * dy);
+                o.x = dx - a.model.eta * (gg[t].x + f2v(a.model, p[t].x) * dx);
+                o.y = dy - a.model.eta * (gg[t].y + f2v(a.model, p[t].y) * dy);
             } else {
-                o.x = f2v(a.model, p.x) * dx;
-                o.y = f2v(a.model, p.y) * dy;
+                o.x = f2v(a.model, p[t].x) * dx;
+                o.y = f2v(a.model, p[t].y) * dy;
             }
         }
         buf[n * LD + l] = o;
@@ -283,9 +322,11 @@ __global__ void __launch_bounds__(x_nt(M)) k_xmid(XmArgs<T> a) {
     __syncthreads();
     fft_lines<T, -1, H, NL, NT>(buf, tw, M);
     r2c_post<T, H, NL, NT>(buf, nyqs, tw, M);
-    for (int w = threadIdx.x; w < H * NL; w += NT) {
-        int k = w % H, l = w / H;
-        int row = row0 + l;
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int w = threadIdx.x + t * NT;
+        const int k = w % H, l = w / H;
+        const int row = row0 + l;
         if (row < a.rows) a.main[(size_t)row * H + k] = buf[k * LD + l];
     }
     for (int l = threadIdx.x; l < NL; l += NT)
@@ -309,12 +350,11 @@ enum ColMode {
 
 struct ColSeg {
     int nlines;        // lines in this segment
-    int lgrp;          // line l -> base (l / lgrp) * lhi + (l % lgrp) * llo
+    int lg_shift;      // line l -> base (l >> lg_shift) * lhi + (l & ((1 << lg_shift) - 1)) * llo
     long long lhi, llo;
     long long es;      // element stride
     int elem_contig;   // 1 if es == 1 (load along elements)
     int kx_const;      // -1: kx = l % H (main); else fixed kx index (nyq: H)
-    int y_div;         // 3D innermost: y index = (l / y_div) ; 2D: 0 (no y line index)
 };
 
 template <typename T> struct ColArgs {
@@ -342,40 +382,42 @@ template <typename T> struct ColArgs {
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
     constexpr int NL = COL_NL, NT = col_nt(M), LD = NL + 1, H = M / 2;
+    constexpr int IT = (M * NL + NT - 1) / NT;
+    constexpr int HSH = (H >= 256) ? 8 : (H >= 128) ? 7 : (H >= 64) ? 6 : (H >= 32) ? 5 : (H >= 16) ? 4 : (H >= 8) ? 3 : 2;
+    static_assert((1 << HSH) == H, "H must be a power of two");
+    static_assert(NT % NL == 0, "each thread keeps one line in the line-major mapping");
     using C = cplx<T>;
+    constexpr bool PRE = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN);
+    constexpr bool POST = (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT ||
+                           MODE == C_TOP_OUT);
+    constexpr bool AUX = (MODE == C_IMEX_OUT || MODE == C_TOP_OUT);
+    constexpr bool NEED_Q = PRE || (POST && MODE != C_IMEX_OUT);
     if (a.done && *(volatile const int*)a.done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + M;
     T* qt = reinterpret_cast<T*>(buf + M * LD);
     double* red = reinterpret_cast<double*>(qt + 3 * M);
-    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
-    constexpr bool NEED_Q = (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_IN ||
-                             MODE == C_TOP_OUT || MODE == C_MSCALE_IN);
-    if (NEED_Q)
-        for (int i = threadIdx.x; i < 3 * M; i += NT) qt[i] = a.qtab[i];
+    const C zero = mk<T>((T)0, (T)0);
 
     const int segi = blockIdx.x < a.nb_main ? 0 : 1;
     const ColSeg s = a.seg[segi];
     const int l0 = (segi == 0 ? blockIdx.x : blockIdx.x - a.nb_main) * NL;
-    const C* in_main = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) ? a.src_main : a.main;
-    const C* in_nyq = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) ? a.src_nyq : a.nyq;
-    const C* src = segi == 0 ? in_main : in_nyq;
-    C* dst = (MODE == C_IMEX_IN || MODE == C_IMEX_OUT || MODE == C_TOP_OUT || MODE == C_MSCALE_IN)
-                 ? (segi == 0 ? a.dst_main : a.dst_nyq) : (segi == 0 ? a.main : a.nyq);
-    const C* aux = segi == 0 ? a.src_main : a.src_nyq;   // old b / q for *_OUT modes
-
-    auto addr = [&](int l, int e) -> long long {
-        return (long long)(l / s.lgrp) * s.lhi + (long long)(l % s.lgrp) * s.llo + (long long)e * s.es;
+    const C* src = PRE ? (segi == 0 ? a.src_main : a.src_nyq) : (segi == 0 ? a.main : a.nyq);
+    C* dst = (PRE || AUX) ? (segi == 0 ? a.dst_main : a.dst_nyq) : (segi == 0 ? a.main : a.nyq);
+    const C* aux = segi == 0 ? a.src_main : a.src_nyq;
+    const int nval = s.nlines - l0 < NL ? s.nlines - l0 : NL;
+    const long long lmask = (1LL << s.lg_shift) - 1;
+    auto base = [&](int l) -> long long {
+        return (long long)(l >> s.lg_shift) * s.lhi + (long long)(l & lmask) * s.llo;
     };
-    // |Bk|^2 pieces and Hermitian weight of element (l, e) on the innermost axis
-    auto kinfo = [&](int l, int e, T& bk2, T& wgt, bool& is0) {
-        int kx = s.kx_const >= 0 ? s.kx_const : (l % H);
-        T bx = qt[kx];
+    // wavenumber data of element (global line L, element e) of the innermost axis
+    auto kinfo = [&](int L, int e, T& bk2, T& wgt, bool& is0) {
+        const int kx = s.kx_const >= 0 ? s.kx_const : (L & (H - 1));
         T by, bz;
         bool zero_other;
         if (a.dim == 3) {
-            int y = s.kx_const >= 0 ? l : l / H;
+            const int y = s.kx_const >= 0 ? L : (L >> HSH);
             by = qt[M + y];
             bz = qt[2 * M + e];
             zero_other = (y == 0);
@@ -384,103 +426,135 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
             bz = (T)0;
             zero_other = true;
         }
-        bk2 = bx + by + bz;
+        bk2 = qt[kx] + by + bz;
         wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
         is0 = (s.kx_const < 0) && kx == 0 && zero_other && e == 0;
     };
 
-    // load the tile
-    const int nval = s.nlines - l0 < NL ? s.nlines - l0 : NL;
+    // line-major mapping: each thread keeps line l = tid % NL and walks elements
+    const int lm_l = threadIdx.x % NL;
+    const int lm_e0 = threadIdx.x / NL;
+    constexpr int LM_ESTEP = NT / NL;
+    const bool lm_ok = lm_l < nval;
+    const long long lm_base = lm_ok ? base(l0 + lm_l) : 0;
+
+    // 1. issue all loads of the tile (and of the auxiliary spectrum)
+    C v[IT], x[AUX ? IT : 1];
     if (s.elem_contig) {
-        for (int w = threadIdx.x; w < M * NL; w += NT) {
-            int e = w % M, l = w / M;
-            buf[e * LD + l] = l < nval ? src[addr(l0 + l, e)] : mk<T>((T)0, (T)0);
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int w = threadIdx.x + t * NT;
+            const int e = w % M, l = w / M;
+            v[t] = (w < M * NL && l < nval) ? src[base(l0 + l) + e] : zero;
         }
     } else {
-        for (int w = threadIdx.x; w < M * NL; w += NT) {
-            int l = w % NL, e = w / NL;
-            buf[e * LD + l] = l < nval ? src[addr(l0 + l, e)] : mk<T>((T)0, (T)0);
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int e = lm_e0 + t * LM_ESTEP;
+            v[t] = (e < M && lm_ok) ? src[lm_base + (long long)e * s.es] : zero;
         }
+    }
+    if (AUX) {
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int e = lm_e0 + t * LM_ESTEP;
+            x[AUX ? t : 0] = (e < M && lm_ok) ? aux[lm_base + (long long)e * s.es] : zero;
+        }
+    }
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    if (NEED_Q)
+        for (int i = threadIdx.x; i < 3 * M; i += NT) qt[i] = a.qtab[i];
+    T lamv = (T)0;
+    if (MODE == C_IMEX_IN) lamv = (T)(*a.lam);
+    if (PRE) __syncthreads();     // qt ready for the scaling below
+
+    // 2. (optional pre-scaling) and stage the tile in shared memory
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        int e, l;
+        if (s.elem_contig) { const int w = threadIdx.x + t * NT; e = w % M; l = w / M; if (w >= M * NL) continue; }
+        else { e = lm_e0 + t * LM_ESTEP; l = lm_l; if (e >= M) continue; }
+        C val = v[t];
+        if (PRE && l < nval) {
+            T bk2, wgt; bool is0;
+            kinfo(l0 + l, e, bk2, wgt, is0);
+            const T tt = (T)1 - bk2;
+            const T lamk = a.xi2 * tt * tt;
+            T f;
+            if (MODE == C_IMEX_IN) f = a.kscale / ((T)1 + a.eta * (lamk + lamv));
+            else f = a.kscale / sqrt(lamk + a.sigma);
+            val = is0 ? zero : mk<T>(val.x * f, val.y * f);
+        }
+        buf[e * LD + l] = val;
     }
     __syncthreads();
 
     constexpr int NQ = (MODE == C_IMEX_OUT) ? 2 : 1;
     Acc<T> acc[NQ];
-
-    if (MODE == C_IMEX_IN || MODE == C_MSCALE_IN) {
-        T lamv = (MODE == C_IMEX_IN) ? (T)(*a.lam) : (T)0;
-        for (int w = threadIdx.x; w < M * NL; w += NT) {
-            int l = w % NL, e = w / NL;
-            if (l >= nval) continue;
-            T bk2, wgt; bool is0;
-            kinfo(l0 + l, e, bk2, wgt, is0);
-            T t = (T)1 - bk2;
-            T lamk = a.xi2 * t * t;
-            T f;
-            if (MODE == C_IMEX_IN) f = a.kscale / ((T)1 + a.eta * (lamk + lamv));
-            else f = a.kscale / sqrt(lamk + a.sigma);
-            C v = buf[e * LD + l];
-            buf[e * LD + l] = is0 ? mk<T>((T)0, (T)0) : mk<T>(v.x * f, v.y * f);
-        }
-        __syncthreads();
-        fft_lines<T, +1, M, NL, NT>(buf, tw, M);
-    } else if (MODE == C_INV) {
+    // 3. transform, with the reciprocal-space operation of the innermost axis
+    if (PRE || MODE == C_INV) {
         fft_lines<T, +1, M, NL, NT>(buf, tw, M);
     } else {
         fft_lines<T, -1, M, NL, NT>(buf, tw, M);
-        if (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT || MODE == C_TOP_OUT) {
-            for (int w = threadIdx.x; w < M * NL; w += NT) {
-                int l = w % NL, e = w / NL;
-                if (l >= nval) continue;
-                C v = buf[e * LD + l];
+        if (POST) {
+#pragma unroll
+            for (int t = 0; t < IT; ++t) {
+                const int e = lm_e0 + t * LM_ESTEP;
+                if (e >= M || !lm_ok) continue;
+                C val = buf[e * LD + lm_l];
                 T bk2, wgt; bool is0;
-                if (MODE != C_IMEX_OUT) kinfo(l0 + l, e, bk2, wgt, is0);
-                else {
-                    int kx = s.kx_const >= 0 ? s.kx_const : ((l0 + l) % H);
-                    bool zo = (a.dim == 3) ? ((s.kx_const >= 0 ? (l0 + l) : (l0 + l) / H) == 0) : true;
+                if (MODE != C_IMEX_OUT) {
+                    kinfo(l0 + lm_l, e, bk2, wgt, is0);
+                } else {
+                    const int L = l0 + lm_l;
+                    const int kx = s.kx_const >= 0 ? s.kx_const : (L & (H - 1));
+                    const bool zo = (a.dim == 3) ? ((s.kx_const >= 0 ? L : (L >> HSH)) == 0) : true;
                     wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
                     is0 = (s.kx_const < 0) && kx == 0 && zo && e == 0;
                     bk2 = (T)0;
                 }
-                if (is0) v = mk<T>((T)0, (T)0);
+                if (is0) val = zero;
                 if (MODE == C_IMEX_OUT) {
-                    C old = aux[addr(l0 + l, e)];
-                    T dx = old.x - v.x, dy = old.y - v.y;
+                    const C old = x[AUX ? t : 0];
+                    const T dx = old.x - val.x, dy = old.y - val.y;
                     acc[0].add(wgt * (dx * dx + dy * dy));
-                    acc[NQ - 1].add(wgt * (v.x * v.x + v.y * v.y));
-                    buf[e * LD + l] = v;
+                    acc[NQ - 1].add(wgt * (val.x * val.x + val.y * val.y));
+                    buf[e * LD + lm_l] = val;
                     continue;
                 }
-                T t = (T)1 - bk2;
-                T lamk = a.xi2 * t * t;
-                if (MODE == C_LAM_E || MODE == C_QUAD_E) acc[0].add((T)0.5 * wgt * lamk * (v.x * v.x + v.y * v.y));
+                const T tt = (T)1 - bk2;
+                const T lamk = a.xi2 * tt * tt;
+                if (MODE == C_LAM_E || MODE == C_QUAD_E) acc[0].add((T)0.5 * wgt * lamk * (val.x * val.x + val.y * val.y));
                 if (MODE == C_TOP_OUT) {
-                    C q = aux[addr(l0 + l, e)];
-                    T ms = (T)1 / sqrt(lamk + a.sigma);
-                    T c1 = lamk * ms * ms, c2 = ms * a.kscale;
-                    v = is0 ? mk<T>((T)0, (T)0) : mk<T>(c1 * q.x + c2 * v.x, c1 * q.y + c2 * v.y);
+                    const C q = x[AUX ? t : 0];
+                    const T ms = (T)1 / sqrt(lamk + a.sigma);
+                    const T c1 = lamk * ms * ms, c2 = ms * a.kscale;
+                    val = is0 ? zero : mk<T>(c1 * q.x + c2 * val.x, c1 * q.y + c2 * val.y);
                 } else {
-                    T f = lamk * a.kscale;
-                    v = mk<T>(v.x * f, v.y * f);
+                    const T f = lamk * a.kscale;
+                    val = mk<T>(val.x * f, val.y * f);
                 }
-                buf[e * LD + l] = v;
+                buf[e * LD + lm_l] = val;
             }
             __syncthreads();
             if (MODE == C_LAM || MODE == C_LAM_E) fft_lines<T, +1, M, NL, NT>(buf, tw, M);
         }
     }
 
-    // store
+    // 4. store
     if (MODE != C_QUAD_E) {
         if (s.elem_contig) {
-            for (int w = threadIdx.x; w < M * NL; w += NT) {
-                int e = w % M, l = w / M;
-                if (l < nval) dst[addr(l0 + l, e)] = buf[e * LD + l];
+#pragma unroll
+            for (int t = 0; t < IT; ++t) {
+                const int w = threadIdx.x + t * NT;
+                const int e = w % M, l = w / M;
+                if (w < M * NL && l < nval) dst[base(l0 + l) + e] = buf[e * LD + l];
             }
         } else {
-            for (int w = threadIdx.x; w < M * NL; w += NT) {
-                int l = w % NL, e = w / NL;
-                if (l < nval) dst[addr(l0 + l, e)] = buf[e * LD + l];
+#pragma unroll
+            for (int t = 0; t < IT; ++t) {
+                const int e = lm_e0 + t * LM_ESTEP;
+                if (e < M && lm_ok) dst[lm_base + (long long)e * s.es] = buf[e * LD + lm_l];
             }
         }
     }

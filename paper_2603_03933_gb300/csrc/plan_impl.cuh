@@ -240,15 +240,16 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     a.src_main = src; a.src_nyq = src ? src + (size_t)rows_ * h_ : nullptr;
     a.tw = d_tw_; a.qtab = d_qtab_;
     ColSeg s0{}, s1{};
+    auto lg = [](long long v) { int k = 0; while ((1LL << k) < v) ++k; return k; };
     if (dim_ == 3 && axis == 1) {
-        s0 = ColSeg{(int)(M * H), (int)H, M * H, 1, H, 0, -1, 0};
-        s1 = ColSeg{(int)M, 1, M, 0, 1, 1, (int)H, 0};
+        s0 = ColSeg{(int)(M * H), lg(H), M * H, 1, H, 0, -1};
+        s1 = ColSeg{(int)M, 0, M, 0, 1, 1, (int)H};
     } else if (dim_ == 3) {
-        s0 = ColSeg{(int)(M * H), (int)(M * H), 0, 1, M * H, 0, -1, 0};
-        s1 = ColSeg{(int)M, (int)M, 0, 1, M, 0, (int)H, 0};
+        s0 = ColSeg{(int)(M * H), lg(M * H), 0, 1, M * H, 0, -1};
+        s1 = ColSeg{(int)M, lg(M), 0, 1, M, 0, (int)H};
     } else {
-        s0 = ColSeg{(int)H, (int)H, 0, 1, H, 0, -1, 0};
-        s1 = ColSeg{1, 1, 0, 0, 1, 1, (int)H, 0};
+        s0 = ColSeg{(int)H, lg(H), 0, 1, H, 0, -1};
+        s1 = ColSeg{1, 0, 0, 0, 1, 1, (int)H};
     }
     a.seg[0] = s0; a.seg[1] = s1;
     a.nb_main = (s0.nlines + COL_NL - 1) / COL_NL;
