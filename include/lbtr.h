@@ -149,7 +149,7 @@ lb_status lb_tr_subproblem(lb_ctx *ctx, const void *phi, const void *g, double r
                            lb_sub_info *info, lb_stream stream);
 
 typedef struct {
-    int max_steps;     /* Lanczos steps cap (basis vectors kept: max_steps + 1) */
+    int max_steps;     /* Lanczos steps cap, 2..600 (basis vectors kept: max_steps + 1) */
     double tol;        /* stop when the Ritz residual ||H u - theta u|| <= tol */
     double sigma;      /* shift of the congruence M = Lambda + sigma; <= 0 picks
                           max(1e-2, max_x |F''(phi(x))|) */

@@ -196,7 +196,8 @@ lb_status lb_lambda_min(lb_ctx* ctx, const void* phi, const lb_eig_opts* opts, v
     lb_eig_opts o;
     lb_default_eig_opts(&o);
     if (opts) o = *opts;
-    if (o.max_steps < 2) return fail(ctx, LB_ERR_INVALID_ARG, "lb_lambda_min: max_steps must be >= 2");
+    if (o.max_steps < 2 || o.max_steps > 600)
+        return fail(ctx, LB_ERR_INVALID_ARG, "lb_lambda_min: max_steps must be in [2, 600]");
     if (o.check_every < 1) o.check_every = 10;
     lb_eig_info inf;
     std::memset(&inf, 0, sizeof(inf));

@@ -208,6 +208,15 @@ __global__ void k_axpby(T* y, const T* x, double alpha, double beta, const doubl
         y[i] = a * x[i] + (beta == 0.0 ? (T)0 : b * y[i]);
 }
 
+// y -= (*c) * scale  (a device scalar, e.g. a mean from a reduction slot)
+template <typename T>
+__global__ void k_sub_scalar(T* y, const double* c, double scale, long long n) {
+    const T v = (T)(*c * scale);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] -= v;
+}
+
 // Precision conversion and shift: dst = (TD)src + add (add may be null)
 template <typename TD, typename TS>
 __global__ void k_convert(TD* dst, const TS* src, long long n) {

@@ -21,14 +21,18 @@ struct lb_ctx {
     void* scratch = nullptr;             // field-sized temporaries
     size_t scratch_bytes = 0;
     double* d_scal = nullptr;            // small device scalars
-    void* tmp_w[2] = {nullptr, nullptr}; // two working-type fields
-    double* f64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // FP64 fields of the outer loop
+    static constexpr int NW = 8, NF = 8;
+    void* tmp_w[NW] = {};                // working-type fields
+    double* f64[NF] = {};                // FP64 fields of the outer loop
+    void* lz_base = nullptr;             // Lanczos basis and its scratch (allocated on first use)
+    size_t lz_bytes = 0;
     lbtr::Prof prof;                     // per-kernel-class event timing (profiling aid)
 
     ~lb_ctx() {
         delete p64;
         delete p32;
         if (scratch) cudaFree(scratch);
+        if (lz_base) cudaFree(lz_base);
     }
 
     long long n() const { return p64->n(); }
@@ -45,7 +49,7 @@ struct lb_ctx {
         const size_t nn = (size_t)p64->n();
         const size_t wsz = prec == LB_FP64 ? sizeof(double) : sizeof(float);
         auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-        scratch_bytes = up(64 * sizeof(double)) + 2 * up(nn * wsz) + 6 * up(nn * sizeof(double));
+        scratch_bytes = up(64 * sizeof(double)) + NW * up(nn * wsz) + NF * up(nn * sizeof(double));
         if (cudaMalloc(&scratch, scratch_bytes) != cudaSuccess) {
             scratch = nullptr;
             err = "cudaMalloc of the context scratch failed";
@@ -55,8 +59,8 @@ struct lb_ctx {
         char* b = static_cast<char*>(scratch);
         d_scal = reinterpret_cast<double*>(b);
         b += up(64 * sizeof(double));
-        for (int i = 0; i < 2; ++i) { tmp_w[i] = b; b += up(nn * wsz); }
-        for (int i = 0; i < 6; ++i) { f64[i] = reinterpret_cast<double*>(b); b += up(nn * sizeof(double)); }
+        for (int i = 0; i < NW; ++i) { tmp_w[i] = b; b += up(nn * wsz); }
+        for (int i = 0; i < NF; ++i) { f64[i] = reinterpret_cast<double*>(b); b += up(nn * sizeof(double)); }
         return 0;
     }
 
@@ -142,7 +146,7 @@ struct lb_ctx {
         p.imex_final(d, s);
         if ((st = launch_status("lb_tr_subproblem/final"))) return st;
         // ||d|| and f(d) = <g,d> + <d,Hd>/2
-        T* hd = static_cast<T*>(tmp_w[0]);
+        T* hd = static_cast<T*>(tmp_w[7]);
         p.hessvec(phi, d, hd, s);
         p.phys_reduce(lbtr::R_DOT, g, d, lbtr::S_RED0, s);
         double gd[1], dhd[1], dd[2];
@@ -167,6 +171,23 @@ struct lb_ctx {
     template <typename T>
     lb_status lambda_min(lbtr::Plan<T>& p, const T* phi, const lb_eig_opts& o, T* vec, lb_eig_info* info,
                          cudaStream_t s);
+
+    // ||x||^2 (sum over points / N) and related helpers on physical fields
+    template <typename T> lb_status dot(lbtr::Plan<T>& p, const T* x, const T* y, double* out, cudaStream_t s) {
+        p.phys_reduce(lbtr::R_DOT, x, y, lbtr::S_RED0, s);
+        double v;
+        lb_status st = sync_read(&v, p.slot(lbtr::S_RED0), 1, s, "dot");
+        *out = v / (double)p.n();
+        return st;
+    }
+
+    // (H + shift I) x = -g by preconditioned CG; returns ||x|| in *xnorm
+    template <typename T>
+    lb_status pcg(lbtr::Plan<T>& p, const T* phi, const T* g, double shift, double rtol, int max_iter, T* x,
+                  double* xnorm, int* iters, cudaStream_t s);
+
+    template <typename T> lb_status random_ball(lbtr::Plan<T>& p, T* out, double r, unsigned long long seed,
+                                                unsigned stream, cudaStream_t s);
 
     lb_status tr_solve(double* phi, const lb_tr_opts& o, lb_tr_info* info, cudaStream_t s);
 };

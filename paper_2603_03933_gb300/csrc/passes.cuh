@@ -346,6 +346,7 @@ enum ColMode {
     C_IMEX_OUT = 6,  // fwd, zero k0, store dst; reduce sum w |bold - X|^2 and sum w |X|^2 (* escale)
     C_TOP_OUT = 7,   // fwd of T-part, combine out = msc * (Lambda * msc * q + X * kscale), zero k0
     C_MSCALE_IN = 8, // load q, * msc * kscale, zero k0, inv, store dst
+    C_SOLVE = 9,     // fwd, * kscale / (Lambda + sigma), zero k0, inv   (PCG preconditioner)
 };
 
 struct ColSeg {
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
     using C = cplx<T>;
     constexpr bool PRE = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN);
     constexpr bool POST = (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT ||
-                           MODE == C_TOP_OUT);
+                           MODE == C_TOP_OUT || MODE == C_SOLVE);
     constexpr bool AUX = (MODE == C_IMEX_OUT || MODE == C_TOP_OUT);
     constexpr bool NEED_Q = PRE || (POST && MODE != C_IMEX_OUT);
     if (a.done && *(volatile const int*)a.done) return;
@@ -530,6 +531,9 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
                     const T ms = (T)1 / sqrt(lamk + a.sigma);
                     const T c1 = lamk * ms * ms, c2 = ms * a.kscale;
                     val = is0 ? zero : mk<T>(c1 * q.x + c2 * val.x, c1 * q.y + c2 * val.y);
+                } else if (MODE == C_SOLVE) {
+                    const T f = a.kscale / (lamk + a.sigma);
+                    val = is0 ? zero : mk<T>(val.x * f, val.y * f);
                 } else {
                     const T f = lamk * a.kscale;
                     val = mk<T>(val.x * f, val.y * f);
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
                 buf[e * LD + lm_l] = val;
             }
             __syncthreads();
-            if (MODE == C_LAM || MODE == C_LAM_E) fft_lines<T, +1, M, NL, NT>(buf, tw, M);
+            if (MODE == C_LAM || MODE == C_LAM_E || MODE == C_SOLVE) fft_lines<T, +1, M, NL, NT>(buf, tw, M);
         }
     }
 
@@ -565,6 +569,22 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
             for (int q = 0; q < NQ; ++q) tot[q] *= a.escale;
         finalize_partials(a.red, tot);
     }
+}
+
+// sum_x s^2 (F''(v)/2 + F'''(v) s/6 + s^2/24) = sum_x [F(v+s) - F(v) - F'(v) s]: the
+// exact Taylor remainder of the quartic bulk density, free of cancellation.
+template <typename T>
+__global__ void k_taylor_rem(const T* v, const T* sd, long long n, Model<T> m, RedSlot red) {
+    __shared__ double scr[64];
+    Acc<T> acc[1];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T u = v[i], s = sd[i];
+        acc[0].add(s * s * (f2v(m, u) * (T)0.5 + (u - m.gamma) * s * (T)(1.0 / 6.0) + s * s * (T)(1.0 / 24.0)));
+    }
+    double tot[1];
+    block_sum<T, 1>(acc, scr, tot);
+    finalize_partials(red, tot);
 }
 
 }  // namespace lbtr

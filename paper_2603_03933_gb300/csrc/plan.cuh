@@ -7,6 +7,7 @@
 #include "aux_kernels.cuh"
 #include "passes.cuh"
 #include "prof.cuh"
+#include "spec_kernels.cuh"
 
 namespace lbtr {
 
@@ -65,6 +66,18 @@ public:
     void to_spectrum(const T* x, C* out, cudaStream_t s);
     // paper-normalised half spectrum -> physical; with msc: apply M^{-1/2} first
     void from_spectrum(const C* q, T* x, bool msc, double sigma, cudaStream_t s);
+
+    // out = F^{-1}[(Lambda + shift)^{-1} F x] with the k = 0 mode removed (PCG preconditioner)
+    void precond(const T* x, T* out, double shift, cudaStream_t s);
+    // sum_x s^2 (F''(v)/2 + F'''(v) s/6 + s^2/24) into slot
+    void taylor_rem(const T* v, const T* sd, int slot, cudaStream_t s);
+    // y = a x + b y on physical fields
+    void axpby(T* y, const T* x, double a, double b, cudaStream_t s);
+    // y -= (*c) * scale
+    void sub_scalar(T* y, const double* c, double scale, cudaStream_t s);
+    // i.i.d. N(0,1) samples from Philox4x32-10 (seed, stream)
+    void random_normal(T* out, unsigned long long seed, unsigned stream, cudaStream_t s);
+    int max_blocks() const { return max_blocks_; }
 
     // barrier / error bookkeeping
     void set_barrier_budget(long long cycles) { budget_ = cycles > 0 ? cycles : kDefaultBudget; }

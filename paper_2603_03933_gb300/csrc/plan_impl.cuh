@@ -67,6 +67,7 @@ template <typename T, int M> cudaError_t set_smem_attrs() {
     setc((const void*)k_cols<T, M, C_IMEX_OUT>);
     setc((const void*)k_cols<T, M, C_TOP_OUT>);
     setc((const void*)k_cols<T, M, C_MSCALE_IN>);
+    setc((const void*)k_cols<T, M, C_SOLVE>);
     return e;
 }
 
@@ -269,6 +270,7 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
             case C_IMEX_IN: launch_cols<T, M, C_IMEX_IN>(a, grid, s); break;
             case C_IMEX_OUT: launch_cols<T, M, C_IMEX_OUT>(a, grid, s); break;
             case C_TOP_OUT: launch_cols<T, M, C_TOP_OUT>(a, grid, s); break;
+            case C_SOLVE: launch_cols<T, M, C_SOLVE>(a, grid, s); break;
             default: launch_cols<T, M, C_MSCALE_IN>(a, grid, s); break;
         }
     });
@@ -429,6 +431,41 @@ template <typename T> void Plan<T>::kop(const T* phi, const C* q, C* out, double
     xmid(XM_TOP, d_work2_, phi, nullptr, (T)1, s);
     if (dim_ == 3) cols(1, C_FWD, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
     cols(inner, C_TOP_OUT, d_work2_, out, q, (T)(1.0 / (double)n_), 0.0, sigma, nullptr, S_RED0, s);
+}
+
+template <typename T> void Plan<T>::precond(const T* x, T* out, double shift, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work2_, S_RED0, s);
+    if (dim_ == 3) cols(1, C_FWD, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    cols(inner, C_SOLVE, d_work2_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, shift, nullptr, S_RED0, s);
+    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    xinv(XI_PLAIN, d_work2_, out, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+}
+
+template <typename T> void Plan<T>::taylor_rem(const T* v, const T* sd, int slot, cudaStream_t s) {
+    int grid = (int)std::min<long long>(max_blocks_, (n_ + 255) / 256);
+    if (grid < 1) grid = 1;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    k_taylor_rem<T><<<grid, 256, 0, s>>>(v, sd, n_, model_, redslot(slot, 1, 0u));
+    if (prof_) prof_->end(K_REDUCE, e0, s, 2 * fb());
+}
+
+template <typename T> void Plan<T>::axpby(T* y, const T* x, double a, double b, cudaStream_t s) {
+    int grid = (int)std::min<long long>(4 * max_blocks_, (n_ + 255) / 256);
+    if (grid < 1) grid = 1;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    k_axpby<T><<<grid, 256, 0, s>>>(y, x, a, b, nullptr, 0.0, n_);
+    if (prof_) prof_->end(K_REDUCE, e0, s, (b == 0.0 ? 2 : 3) * fb());
+}
+
+template <typename T> void Plan<T>::sub_scalar(T* y, const double* c, double scale, cudaStream_t s) {
+    int grid = (int)std::min<long long>(4 * max_blocks_, (n_ + 255) / 256);
+    k_sub_scalar<T><<<grid, 256, 0, s>>>(y, c, scale, n_);
+}
+
+template <typename T> void Plan<T>::random_normal(T* out, unsigned long long seed, unsigned stream, cudaStream_t s) {
+    int grid = (int)std::min<long long>(4 * max_blocks_, (n_ / 2 + 255) / 256 + 1);
+    k_philox_normal<T><<<grid, 256, 0, s>>>(out, n_, seed, stream);
 }
 
 template <typename T> int Plan<T>::read_error(cudaStream_t s) {

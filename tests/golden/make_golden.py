@@ -1,0 +1,60 @@
+"""Write the oracle's whole-solve results used by the GPU tests (calls only oracle/).
+
+Usage: python tests/golden/make_golden.py [name ...]
+Each entry runs the FP64 oracle's Algorithm 1 (with Algorithms 2 and 3) from a seeded
+input and stores the converged energy, max|g| and the smallest Hessian eigenvalue.
+"""
+import json
+import math
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import eig, lb, trust_region as tr  # noqa: E402
+from paper_2603_03933_gb300 import inputs  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_solves.json")
+
+
+def case_2d_16():
+    w = inputs.random_problem((16, 16), 5, sigma=0.05, tau=-0.2, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    return w, dict(eps=1e-8, max_outer=100, max_inner=20000)
+
+
+def case_2d_64_plain():
+    # 2D LB, 64^2, box 8 pi, xi = 1, tau = -0.15, gamma = 0.25, phi0 ~ N(0, 0.1^2): to ||g||_inf < 1e-8
+    w = inputs.config_2d_plain(64)
+    return w, dict(eps=1e-8, max_outer=200, max_inner=20000)
+
+
+CASES = {"2d_16_nonconvex": case_2d_16, "2d_64_plain": case_2d_64_plain}
+
+
+def run(name):
+    w, kw = CASES[name]()
+    p = lb.Problem.from_workload(w)
+    t0 = time.time()
+    log = []
+    out = tr.imex_tr(p, w.phi0, log=log, **kw)
+    lam = out["lambda_min"]
+    if lam is None:
+        lam = eig.lanczos_lambda_min(p, out["v"], k_max=300, tol=1e-8)["theta"]
+    return {"workload": w.name, "energy": out["E"], "gmax": out["gmax"], "lambda_min": lam,
+            "status": out["status"], "outer": out["outer"], "inner": out["inner"],
+            "oracle_seconds": time.time() - t0, "params": kw}
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or list(CASES)
+    data = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            data = json.load(f)
+    for n in names:
+        data[n] = run(n)
+        with open(OUT, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        print(n, data[n], flush=True)

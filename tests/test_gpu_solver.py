@@ -1,0 +1,135 @@
+"""GPU tests of lb_lambda_min and lb_imex_tr_solve against the oracle (through the C ABI)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import eig as oeig
+from oracle import lb as olb
+from paper_2603_03933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_solves.json")
+
+
+@pytest.fixture(scope="module")
+def lbtr():
+    from paper_2603_03933_gb300 import build, lbtr as mod
+    build.build(force=False)
+    mod.load()
+    return mod
+
+
+def _ctx(lbtr, w, prec):
+    return lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, prec)
+
+
+@pytest.mark.parametrize("sig,tau", [(0.05, -0.2), (0.6, -0.05)])
+def test_lambda_min_matches_dense_fp64(lbtr, sig, tau):
+    w = inputs.random_problem((16, 16), 8, sigma=sig, tau=tau, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    p = olb.Problem.from_workload(w)
+    s, _ = oeig.dense_eigs(p, w.phi0, count=2)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    vec = torch.empty_like(phi)
+    o = lbtr.default_eig_opts()
+    o.max_steps = 255
+    o.tol = 1e-7
+    info = lbtr.lb_lambda_min(ctx, phi, vec=vec, opts=o, raise_on_noconv=False)
+    assert info["lambda_min"] >= s[0] - 1e-9            # Rayleigh-Ritz upper bound
+    assert abs(info["lambda_min"] - s[0]) <= 1e-8 * max(1.0, abs(s[0]))
+    assert np.sign(info["kappa_min"]) == np.sign(s[0])  # congruence keeps the inertia
+    u = vec.cpu().numpy()
+    assert abs(olb.norm(u) - 1.0) < 1e-10
+    # the returned vector is an approximate eigenvector of the oracle's H
+    r = olb.hessvec(p, w.phi0, u) - info["lambda_min"] * u
+    assert olb.norm(r) <= max(1e-6, 2 * info["residual"])
+
+
+def test_lambda_min_zero_field_closed_form(lbtr):
+    # phi = 0: H = D + tau I, lambda_min = tau + min_{k != 0} Lambda_k (= tau here: |Bk| = 1 exists)
+    shape, box = (32, 32), (2 * math.pi, 2 * math.pi)
+    w = inputs.Workload("zero", shape, box, 1.0, -0.3, 0.2, np.zeros(shape))
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    phi = torch.zeros(shape, dtype=torch.float64, device=DEV)
+    info = lbtr.lb_lambda_min(ctx, phi, raise_on_noconv=False)
+    assert abs(info["lambda_min"] - (-0.3)) < 1e-9
+
+
+@pytest.mark.parametrize("shape,box", [((32, 32), (2 * math.pi, 2 * math.pi)), ((16, 16, 16), (4.0, 5.0, 6.0))])
+def test_lambda_min_matches_oracle_lanczos(lbtr, shape, box):
+    w = inputs.random_problem(shape, 9, sigma=0.1, tau=-0.1, gamma=0.3, box=box)
+    p = olb.Problem.from_workload(w)
+    ref = oeig.lanczos_lambda_min(p, w.phi0, k_max=300, tol=1e-8)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    o = lbtr.default_eig_opts()
+    o.max_steps = 300
+    o.tol = 1e-8
+    info = lbtr.lb_lambda_min(ctx, phi, opts=o, raise_on_noconv=False)
+    assert abs(info["lambda_min"] - ref["theta"]) <= 1e-7 * max(1.0, abs(ref["theta"]))
+
+
+def test_lambda_min_mixed_precision(lbtr):
+    w = inputs.random_problem((32, 32), 9, sigma=0.1, tau=-0.1, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    p = olb.Problem.from_workload(w)
+    phi32 = torch.tensor(w.phi0, dtype=torch.float32, device=DEV)
+    ref = oeig.lanczos_lambda_min(p, phi32.double().cpu().numpy(), k_max=300, tol=1e-8)
+    ctx = _ctx(lbtr, w, lbtr.LB_MIXED)
+    o = lbtr.default_eig_opts()
+    o.tol = 1e-4
+    info = lbtr.lb_lambda_min(ctx, phi32, opts=o, raise_on_noconv=False)
+    assert abs(info["lambda_min"] - ref["theta"]) <= 1e-5 * max(1.0, abs(ref["theta"]))
+    assert np.sign(info["kappa_min"]) == np.sign(ref["theta"])
+
+
+def test_barrier_timeout_returns_status_without_hang(lbtr):
+    # A grid-barrier budget of one cycle makes every waiting block give up at once; the
+    # call must return LB_ERR_TIMEOUT and the context must stay usable afterwards.
+    w = inputs.random_problem((16, 16), 3, sigma=0.3)
+    p = olb.Problem.from_workload(w)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    g = torch.tensor(olb.gradient(p, w.phi0), dtype=torch.float64, device=DEV)
+    d = torch.empty_like(phi)
+    lbtr.lb_set_barrier_budget(ctx, 1)
+    with pytest.raises(lbtr.LBError) as e:
+        lbtr.lb_tr_subproblem(ctx, phi, g, 0.05, d)
+    assert e.value.status == 5
+    lbtr.lb_set_barrier_budget(ctx, 0)
+    info = lbtr.lb_tr_subproblem(ctx, phi, g, 0.05, d)
+    assert info["converged"]
+
+
+def _golden(name):
+    if not os.path.exists(GOLDEN):
+        pytest.skip("oracle golden solves not generated")
+    with open(GOLDEN) as f:
+        data = json.load(f)
+    if name not in data:
+        pytest.skip(f"golden {name} missing")
+    return data[name]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tr_solve_small_matches_oracle(lbtr, prec):
+    ref = _golden("2d_16_nonconvex")
+    w = inputs.random_problem((16, 16), 5, sigma=0.05, tau=-0.2, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    p = olb.Problem.from_workload(w)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    o = lbtr.default_tr_opts()
+    o.eps = 1e-8
+    o.max_outer = 200
+    info = lbtr.lb_imex_tr_solve(ctx, phi, opts=o)
+    v = phi.cpu().numpy()
+    # checks made by the oracle on the returned field
+    assert np.max(np.abs(olb.gradient(p, v))) < 1e-8
+    s, _ = oeig.dense_eigs(p, v, count=1)
+    assert s[0] >= -1e-8                                  # second-order stationary
+    assert abs(info["energy"] - olb.energy(p, v)) < 1e-12
+    assert abs(info["energy"] - ref["energy"]) < 1e-8     # the oracle's own solve
