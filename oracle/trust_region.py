@@ -9,7 +9,7 @@ Readings of the paper taken here (all listed in the design notes):
     with G(s) = 1/2 sum_k Lambda_k |s_hat_k|^2, which avoids the cancellation of a
     difference of two O(1e-2) energies; `energy_drop_direct` keeps the literal form.
   * "||s_j|| = nu_j" is read as | ||s_j|| - nu_j | <= 1e-12 nu_j.
-  * mu: line 6 of Algorithm 1 updates the running mu when the previous ratio failed;
+  * mu: the update Algorithm 1 makes when the previous ratio failed acts on the running mu;
     the CONTRACT branch leaves mu unchanged.
   * CONTRACT's linear systems (H + lambda~ I) s = -g are solved by preconditioned CG
     with preconditioner (Lambda + lambda~ + c)^{-1}, c = max(0, mean F''(psi)); the
