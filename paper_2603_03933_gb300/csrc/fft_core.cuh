@@ -75,10 +75,10 @@ __host__ __device__ constexpr int plan_p(int L, int pass) {
 }
 
 // One Stockham pass of radix R with stride product P on NL lines of length L.
-// Thread tid of NT handles work items w = tid + t NT (line = w % NL, butterfly = w / NL).
-template <typename T, int SIGN, int L, int R, int P, int NL, int NT>
-__device__ __forceinline__ void stockham_pass(cplx<T>* buf, const cplx<T>* tw, int mtab) {
-    constexpr int LD = NL + 1;
+// Element e of line l sits at buf[e * ES + l * LS].  Thread tid of NT handles work
+// items w = tid + t NT (line = w % NL, butterfly = w / NL).
+template <typename T, int SIGN, int L, int R, int P, int NL, int NT, int ES, int LS>
+__device__ __forceinline__ void stockham_pass_s(cplx<T>* buf, const cplx<T>* tw, int mtab) {
     constexpr int NB = L / R;             // butterflies per line
     constexpr int TOT = NB * NL;
     constexpr int IT = (TOT + NT - 1) / NT;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, const cplx<T>* tw, i
             int l = w % NL, i = w / NL;
             int k = i % P;
 #pragma unroll
-            for (int r = 0; r < R; ++r) u[t][r] = buf[(i + r * NB) * LD + l];
+            for (int r = 0; r < R; ++r) u[t][r] = buf[(i + r * NB) * ES + l * LS];
             if (P > 1) {
                 int step = mtab / (P * R);
 #pragma unroll
@@ -114,20 +114,84 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, const cplx<T>* tw, i
             int k = i % P;
             int j = (i - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[(j + r * P) * LD + l] = u[t][r];
+            for (int r = 0; r < R; ++r) buf[(j + r * P) * ES + l * LS] = u[t][r];
         }
     }
     __syncthreads();
 }
 
-// Full in-place DFT of NL lines of length L in shared memory (sign SIGN, unscaled).
-// Requires a __syncthreads() between the producer of buf and this call.
+template <typename T, int SIGN, int L, int R, int P, int NL, int NT>
+__device__ __forceinline__ void stockham_pass(cplx<T>* buf, const cplx<T>* tw, int mtab) {
+    stockham_pass_s<T, SIGN, L, R, P, NL, NT, NL + 1, 1>(buf, tw, mtab);
+}
+
+// Full in-place DFT of NL lines of length L in shared memory (sign SIGN, unscaled),
+// element e of line l at buf[e * ES + l * LS].  Requires a __syncthreads() between
+// the producer of buf and this call.
+template <typename T, int SIGN, int L, int NL, int NT, int ES, int LS>
+__device__ __forceinline__ void fft_lines_s(cplx<T>* buf, const cplx<T>* tw, int mtab) {
+    constexpr int NP = plan_npass(L);
+    stockham_pass_s<T, SIGN, L, plan_radix(L, 0), plan_p(L, 0), NL, NT, ES, LS>(buf, tw, mtab);
+    if (NP > 1) stockham_pass_s<T, SIGN, L, plan_radix(L, NP > 1 ? 1 : 0), plan_p(L, NP > 1 ? 1 : 0), NL, NT, ES, LS>(buf, tw, mtab);
+    if (NP > 2) stockham_pass_s<T, SIGN, L, plan_radix(L, NP > 2 ? 2 : 0), plan_p(L, NP > 2 ? 2 : 0), NL, NT, ES, LS>(buf, tw, mtab);
+}
+
 template <typename T, int SIGN, int L, int NL, int NT>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw, int mtab) {
-    constexpr int NP = plan_npass(L);
-    stockham_pass<T, SIGN, L, plan_radix(L, 0), plan_p(L, 0), NL, NT>(buf, tw, mtab);
-    if (NP > 1) stockham_pass<T, SIGN, L, plan_radix(L, NP > 1 ? 1 : 0), plan_p(L, NP > 1 ? 1 : 0), NL, NT>(buf, tw, mtab);
-    if (NP > 2) stockham_pass<T, SIGN, L, plan_radix(L, NP > 2 ? 2 : 0), plan_p(L, NP > 2 ? 2 : 0), NL, NT>(buf, tw, mtab);
+    fft_lines_s<T, SIGN, L, NL, NT, NL + 1, 1>(buf, tw, mtab);
+}
+
+// After a forward length-H DFT of z[n] = x[2n] + i x[2n+1] on NL lines, turn Z into the
+// real spectrum X[0..H-1] in place and X[H] into the slot at element index H of each
+// line (element stride ES, line stride LS; table W_M of size 2H).
+template <typename T, int H, int NL, int NT, int ES, int LS>
+__device__ __forceinline__ void r2c_post_s(cplx<T>* buf, const cplx<T>* tw, int mtab) {
+    constexpr int NPAIR = H / 2 + 1;        // k = 0..H/2
+    using C = cplx<T>;
+    const int step = mtab / (2 * H);
+    for (int w = threadIdx.x; w < NPAIR * NL; w += NT) {
+        int l = w % NL, k = w / NL;
+        if (k == 0) {
+            C z = buf[l * LS];
+            buf[l * LS] = mk<T>(z.x + z.y, (T)0);
+            buf[H * ES + l * LS] = mk<T>(z.x - z.y, (T)0);
+        } else {
+            C zk = buf[k * ES + l * LS];
+            C zm = buf[(H - k) * ES + l * LS];
+            C e = mk<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+            C o = mk<T>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+            C wo = cmul(tw[k * step], o);
+            buf[k * ES + l * LS] = cadd(e, wo);
+            if (2 * k != H) buf[(H - k) * ES + l * LS] = cconj(csub(e, wo));
+        }
+    }
+    __syncthreads();
+}
+
+// Inverse of r2c_post_s: from X[0..H] (X[H] at element index H) build
+// Z[k] = (X[k] + conj X[H-k]) + i (X[k] - conj X[H-k]) conj(W^k) for k < H.
+template <typename T, int H, int NL, int NT, int ES, int LS>
+__device__ __forceinline__ void c2r_pre_s(cplx<T>* buf, const cplx<T>* tw, int mtab) {
+    constexpr int NPAIR = H / 2 + 1;
+    using C = cplx<T>;
+    const int step = mtab / (2 * H);
+    for (int w = threadIdx.x; w < NPAIR * NL; w += NT) {
+        int l = w % NL, k = w / NL;
+        if (k == 0) {
+            T x0 = buf[l * LS].x, xh = buf[H * ES + l * LS].x;
+            buf[l * LS] = mk<T>(x0 + xh, x0 - xh);
+        } else {
+            C xk = buf[k * ES + l * LS];
+            C xm = buf[(H - k) * ES + l * LS];
+            C e = mk<T>(xk.x + xm.x, xk.y - xm.y);
+            C d = mk<T>(xk.x - xm.x, xk.y + xm.y);
+            C wc = tw[k * step]; wc.y = -wc.y;
+            C o = cmul(d, wc);
+            buf[k * ES + l * LS] = mk<T>(e.x - o.y, e.y + o.x);
+            if (2 * k != H) buf[(H - k) * ES + l * LS] = mk<T>(e.x + o.y, -e.y + o.x);
+        }
+    }
+    __syncthreads();
 }
 
 // After a forward length-H DFT of z[n] = x[2n] + i x[2n+1], turn Z into the real

@@ -112,6 +112,11 @@ private:
     void xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done = nullptr);
     void cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
               const double* lam, int slot, cudaStream_t s, const int* done = nullptr);
+    void fwd_outer(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale, C* spec,
+                   int slot, cudaStream_t s, const int* done = nullptr);
+    void inv_outer(int mode, C* spec, T* out, const T* phi, const T* v, const double* msum, T oscale, int slot,
+                   cudaStream_t s, const int* done = nullptr);
+    void mid_outer(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done = nullptr);
     RedSlot redslot(int slot, int nq, unsigned max_mask);
     void secular(const C* b, int check, int j, cudaStream_t s);
 
@@ -144,6 +149,7 @@ private:
     int max_blocks_ = 0;
     cudaError_t launch_err_ = cudaSuccess;
     Prof* prof_ = nullptr;
+    bool use_planes_ = false;
     double fb() const { return (double)n_ * sizeof(T); }
     double sb() const { return (double)spec_len() * sizeof(C); }
 };

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "plan.cuh"
+#include "planes.cuh"
 
 namespace lbtr {
 
@@ -37,6 +38,36 @@ template <typename T, int M, int MODE> void launch_xmid(const XmArgs<T>& a, int 
 }
 template <typename T, int M, int MODE> void launch_cols(const ColArgs<T>& a, int grid, cudaStream_t s) {
     k_cols<T, M, MODE><<<grid, col_nt(M), col_smem<T>(M), s>>>(a);
+}
+
+template <typename T, int M, int MODE> void launch_pfwd(const XfArgs<T>& a, cudaStream_t s) {
+    if constexpr (M >= 32 && M <= 128) k_plane_fwd<T, M, MODE><<<M, plane_nt(M), plane_smem<T>(M), s>>>(a);
+}
+template <typename T, int M, int MODE> void launch_pinv(const XiArgs<T>& a, cudaStream_t s) {
+    if constexpr (M >= 32 && M <= 128) k_plane_inv<T, M, MODE><<<M, plane_nt(M), plane_smem<T>(M), s>>>(a);
+}
+template <typename T, int M, int MODE> void launch_pmid(const XmArgs<T>& a, cudaStream_t s) {
+    if constexpr (M >= 32 && M <= 128) k_plane_mid<T, M, MODE><<<M, plane_nt(M), plane_smem<T>(M), s>>>(a);
+}
+
+template <typename T, int M> cudaError_t set_plane_attrs() {
+    cudaError_t e = cudaSuccess;
+    if constexpr (M >= 32 && M <= 128) {
+        auto setp = [&](const void* f) {
+            cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<T>(M));
+            if (r != cudaSuccess) e = r;
+        };
+        setp((const void*)k_plane_fwd<T, M, XF_PLAIN>);
+        setp((const void*)k_plane_fwd<T, M, XF_HVPMEAN>);
+        setp((const void*)k_plane_fwd<T, M, XF_ENERGY>);
+        setp((const void*)k_plane_fwd<T, M, XF_IMEX0>);
+        setp((const void*)k_plane_inv<T, M, XI_PLAIN>);
+        setp((const void*)k_plane_inv<T, M, XI_HVP>);
+        setp((const void*)k_plane_inv<T, M, XI_GRAD>);
+        setp((const void*)k_plane_mid<T, M, XM_IMEX>);
+        setp((const void*)k_plane_mid<T, M, XM_TOP>);
+    }
+    return e;
 }
 
 template <typename T, int M> cudaError_t set_smem_attrs() {
@@ -89,6 +120,11 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     cudaError_t ea = cudaSuccess;
     LB_SWITCH_M(m_, ea = set_smem_attrs<T, M>());
     if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+    use_planes_ = (dim_ == 3 && m_ >= 32 && m_ <= 128);
+    if (use_planes_) {
+        LB_SWITCH_M(m_, ea = set_plane_attrs<T, M>());
+        if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+    }
 
     int occ = 0;
     LB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_secular<T>, 256, 3 * m_ * sizeof(T)));
@@ -281,24 +317,94 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     }
 }
 
+// All transforms except the innermost axis, forward (x pass, plus y in 3D).
+template <typename T>
+void Plan<T>::fwd_outer(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
+                        C* spec, int slot, cudaStream_t s, const int* done) {
+    if (!use_planes_) {
+        xfwd(mode, in, phi, g, d0, dscale, spec, slot, s, done);
+        if (dim_ == 3) cols(1, C_FWD, spec, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        return;
+    }
+    XfArgs<T> a;
+    a.in = in; a.phi = phi; a.g = g; a.d0 = d0; a.dscale = dscale;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.tw = d_tw_; a.rows = rows_; a.model = model_; a.model.eta = (T)eta;
+    a.red = redslot(slot, mode == XF_ENERGY ? 4 : 1, 0u);
+    a.done = done;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    LB_SWITCH_M(m_, {
+        if (mode == XF_PLAIN) launch_pfwd<T, M, XF_PLAIN>(a, s);
+        else if (mode == XF_HVPMEAN) launch_pfwd<T, M, XF_HVPMEAN>(a, s);
+        else if (mode == XF_ENERGY) launch_pfwd<T, M, XF_ENERGY>(a, s);
+        else launch_pfwd<T, M, XF_IMEX0>(a, s);
+    });
+    if (prof_) {
+        double nf = mode == XF_HVPMEAN ? 2 : mode == XF_IMEX0 ? (d0 ? 3 : 2) : 1;
+        prof_->end(K_XFWD, e0, s, nf * fb() + sb());
+    }
+}
+
+// All transforms except the innermost axis, inverse, with the x-pass epilogue.
+template <typename T>
+void Plan<T>::inv_outer(int mode, C* spec, T* out, const T* phi, const T* v, const double* msum, T oscale,
+                        int slot, cudaStream_t s, const int* done) {
+    if (!use_planes_) {
+        if (dim_ == 3) cols(1, C_INV, spec, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        xinv(mode, spec, out, phi, v, msum, oscale, slot, s, done);
+        return;
+    }
+    XiArgs<T> a;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.out = out; a.phi = phi; a.v = v; a.msum = msum; a.inv_n = 1.0 / (double)n_; a.oscale = oscale;
+    a.tw = d_tw_; a.rows = rows_; a.model = model_;
+    a.red = redslot(slot, 1, 1u);
+    a.done = done;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    LB_SWITCH_M(m_, {
+        if (mode == XI_PLAIN) launch_pinv<T, M, XI_PLAIN>(a, s);
+        else if (mode == XI_HVP) launch_pinv<T, M, XI_HVP>(a, s);
+        else launch_pinv<T, M, XI_GRAD>(a, s);
+    });
+    if (prof_) prof_->end(K_XINV, e0, s, sb() + (mode == XI_HVP ? 3 : mode == XI_GRAD ? 2 : 1) * fb());
+}
+
+// Inverse outer transforms -> pointwise -> forward outer transforms.
+template <typename T>
+void Plan<T>::mid_outer(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done) {
+    if (!use_planes_) {
+        if (dim_ == 3) cols(1, C_INV, spec, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        xmid(mode, spec, phi, g, scale, s, done);
+        if (dim_ == 3) cols(1, C_FWD, spec, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        return;
+    }
+    XmArgs<T> a;
+    a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
+    a.phi = phi; a.g = g; a.tw = d_tw_; a.rows = rows_; a.scale = scale;
+    a.model = model_; a.model.eta = (T)eta;
+    a.done = done;
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    LB_SWITCH_M(m_, {
+        if (mode == XM_IMEX) launch_pmid<T, M, XM_IMEX>(a, s);
+        else launch_pmid<T, M, XM_TOP>(a, s);
+    });
+    if (prof_) prof_->end(K_XMID, e0, s, 2 * sb() + (mode == XM_IMEX ? 2 : 1) * fb());
+}
+
 template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
-    xfwd(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
     cols(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0, s);
-    if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-    xinv(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
+    inv_outer(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
 }
 
 template <typename T> void Plan<T>::energy_grad(const T* phi, T* grad, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
     const double inv_n = 1.0 / (double)n_;
-    xfwd(XF_ENERGY, phi, phi, nullptr, nullptr, nullptr, d_work_, S_EF, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_ENERGY, phi, phi, nullptr, nullptr, nullptr, d_work_, S_EF, s);
     if (grad) {
         cols(inner, C_LAM_E, d_work_, nullptr, nullptr, (T)inv_n, inv_n * inv_n, 0.0, nullptr, S_EG, s);
-        if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-        xinv(XI_GRAD, d_work_, grad, phi, nullptr, slot(S_EF) + 1, (T)1, S_GMAX, s);
+        inv_outer(XI_GRAD, d_work_, grad, phi, nullptr, slot(S_EF) + 1, (T)1, S_GMAX, s);
     } else {
         cols(inner, C_QUAD_E, d_work_, nullptr, nullptr, (T)1, inv_n * inv_n, 0.0, nullptr, S_EG, s);
     }
@@ -307,8 +413,7 @@ template <typename T> void Plan<T>::energy_grad(const T* phi, T* grad, cudaStrea
 template <typename T> void Plan<T>::quad_energy(const T* x, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
     const double inv_n = 1.0 / (double)n_;
-    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work_, S_RED0, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work_, S_RED0, s);
     cols(inner, C_QUAD_E, d_work_, nullptr, nullptr, (T)1, inv_n * inv_n, 0.0, nullptr, S_QUAD, s);
 }
 
@@ -363,8 +468,7 @@ int Plan<T>::imex_init(const T* phi, const T* g, const T* d0, const double* dsca
     const int inner = dim_ == 3 ? 2 : 1;
     cudaMemsetAsync(d_state_, 0, sizeof(ImexState), s);
     cudaMemsetAsync(d_b_[1], 0, sizeof(C) * spec_len(), s);
-    xfwd(XF_IMEX0, nullptr, phi, g, d0, dscale_dev, d_work_, S_RED0, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_IMEX0, nullptr, phi, g, d0, dscale_dev, d_work_, S_RED0, s);
     const double inv_n = 1.0 / (double)n_;
     cols(inner, C_IMEX_OUT, d_work_, d_b_[0], d_b_[1], (T)1, inv_n * inv_n, 0.0, nullptr, S_IMEX, s);
     secular(d_b_[0], 0, 0, s);
@@ -379,9 +483,7 @@ template <typename T> int Plan<T>::imex_iterate(const T* phi, const T* g, int j0
         C* src = d_b_[(j - 1) & 1];
         C* dst = d_b_[j & 1];
         cols(inner, C_IMEX_IN, nullptr, d_work_, src, (T)inv_n, 0.0, 0.0, &d_state_->lam, S_RED0, s, done);
-        if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
-        xmid(XM_IMEX, d_work_, phi, g, (T)1, s, done);
-        if (dim_ == 3) cols(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s, done);
+        mid_outer(XM_IMEX, d_work_, phi, g, (T)1, s, done);
         cols(inner, C_IMEX_OUT, d_work_, dst, src, (T)1, inv_n * inv_n, 0.0, nullptr, S_IMEX, s, done);
         secular(dst, 1, j, s);
     }
@@ -397,15 +499,13 @@ template <typename T> void Plan<T>::imex_final(T* d, cudaStream_t s) {
     const double inv_n = 1.0 / (double)n_;
     cols(inner, C_IMEX_IN, nullptr, d_work_, d_b_[st.final_src & 1], (T)inv_n, 0.0, 0.0, &d_state_->final_lam,
          S_RED0, s);
-    if (dim_ == 3) cols(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-    xinv(XI_PLAIN, d_work_, d, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+    inv_outer(XI_PLAIN, d_work_, d, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
 }
 
 template <typename T> void Plan<T>::to_spectrum(const T* x, C* out, cudaStream_t s) {
     // paper-normalised coefficients: DFT / N
     const int inner = dim_ == 3 ? 2 : 1;
-    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, out, S_RED0, s);
-    if (dim_ == 3) cols(1, C_FWD, out, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, out, S_RED0, s);
     cols(inner, C_FWD, out, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
     long long len = spec_len() * 2;
     k_axpby<T><<<(int)std::min<long long>(4096, (len + 255) / 256), 256, 0, s>>>(
@@ -420,26 +520,21 @@ template <typename T> void Plan<T>::from_spectrum(const C* q, T* x, bool msc, do
         cudaMemcpyAsync(d_work2_, q, sizeof(C) * spec_len(), cudaMemcpyDeviceToDevice, s);
         cols(inner, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
     }
-    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-    xinv(XI_PLAIN, d_work2_, x, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+    inv_outer(XI_PLAIN, d_work2_, x, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
 }
 
 template <typename T> void Plan<T>::kop(const T* phi, const C* q, C* out, double sigma, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
     cols(inner, C_MSCALE_IN, nullptr, d_work2_, q, (T)1, 0.0, sigma, nullptr, S_RED0, s);
-    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-    xmid(XM_TOP, d_work2_, phi, nullptr, (T)1, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    mid_outer(XM_TOP, d_work2_, phi, nullptr, (T)1, s);
     cols(inner, C_TOP_OUT, d_work2_, out, q, (T)(1.0 / (double)n_), 0.0, sigma, nullptr, S_RED0, s);
 }
 
 template <typename T> void Plan<T>::precond(const T* x, T* out, double shift, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
-    xfwd(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work2_, S_RED0, s);
-    if (dim_ == 3) cols(1, C_FWD, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
+    fwd_outer(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work2_, S_RED0, s);
     cols(inner, C_SOLVE, d_work2_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, shift, nullptr, S_RED0, s);
-    if (dim_ == 3) cols(1, C_INV, d_work2_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, s);
-    xinv(XI_PLAIN, d_work2_, out, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
+    inv_outer(XI_PLAIN, d_work2_, out, nullptr, nullptr, nullptr, (T)1, S_RED0, s);
 }
 
 template <typename T> void Plan<T>::taylor_rem(const T* v, const T* sd, int slot, cudaStream_t s) {
