@@ -230,6 +230,37 @@ def time_hvp(lbtr, ctx, pool, batch, steps, warmup, world):
     return e0.elapsed_time(e1) / 1000.0
 
 
+def time_tr(lbtr, w, prec: str, outer: int) -> dict:
+    """Outer IMEX-TR iterations per second on the workload from its initial field.
+
+    Both precisions solve every subproblem to the same relative residual (1e-6 of
+    ||g||) so the comparison is at equal inner accuracy."""
+    import torch
+    ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
+                                        lbtr.LB_MIXED if prec == "mixed" else lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    o.eps = 1e-8
+    o.sub.eps_sub = 0.0
+    o.sub.rel_tol = 1e-6
+    o.sub.max_iter = 20000
+    o.sub.check_every = 256
+    # warm-up: one short outer iteration
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
+    o.max_outer = 1
+    lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
+    o.max_outer = outer
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n_out = max(1, info["outer"])
+    return {"outer_iters": n_out, "seconds": dt, "tr_iters_per_s": n_out / dt,
+            "inner_iters": info["inner"], "inner_iters_per_s": info["inner"] / dt,
+            "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +273,7 @@ def main():
     ap.add_argument("--only-hvp", action="store_true",
                     help="time only the mixed HVP at --size (small runs for profilers)")
     ap.add_argument("--pool", type=int, default=0, help="override the number of (phi, v, Hv) triples")
+    ap.add_argument("--tr-outer", type=int, default=4, help="outer IMEX-TR iterations timed per precision")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -362,6 +394,12 @@ def main():
         except Exception as ex:  # report, do not hide
             big = {"error": str(ex)}
 
+    # ---- TR iterations (Algorithm 1 outer steps, whole path a1-a9) -------------
+    tr = {}
+    if args.tr_outer > 0:
+        for prec in ("mixed", "fp64"):
+            tr[prec] = time_tr(lbtr, w, prec, args.tr_outer if prec == "mixed" else max(1, args.tr_outer // 2))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_hvp_rate(M)
@@ -377,7 +415,7 @@ def main():
                    "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_hvp * args.batch * args.steps,
-        "fp64": fp64, "size_256": big,
+        "fp64": fp64, "size_256": big, "tr": tr,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -133,3 +133,45 @@ def test_tr_solve_small_matches_oracle(lbtr, prec):
     assert s[0] >= -1e-8                                  # second-order stationary
     assert abs(info["energy"] - olb.energy(p, v)) < 1e-12
     assert abs(info["energy"] - ref["energy"]) < 1e-8     # the oracle's own solve
+
+
+def test_tr_solve_2d_64_plain_matches_oracle(lbtr):
+    # 2D LB, 64^2, box 8 pi, tau -0.15, gamma 0.25, phi0 ~ N(0, 0.1^2): ||g||_inf < 1e-8 and
+    # lambda_min >= -1e-8; energy within 1e-8 of the oracle's own solve
+    ref = _golden("2d_64_plain")
+    w = inputs.config_2d_plain(64)
+    p = olb.Problem.from_workload(w)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    o = lbtr.default_tr_opts()
+    o.eps = 1e-8
+    o.tol2 = 1e-8
+    o.max_outer = 300
+    info = lbtr.lb_imex_tr_solve(ctx, phi, opts=o)
+    v = phi.cpu().numpy()
+    assert np.max(np.abs(olb.gradient(p, v))) < 1e-8
+    assert info["lambda_min"] is not None and info["lambda_min"] >= -1e-8
+    assert abs(info["energy"] - olb.energy(p, v)) < 1e-12
+    assert abs(info["energy"] - ref["energy"]) < 1e-8
+
+
+def test_tr_solve_3d_bcc_mixed_matches_fp64(lbtr):
+    # 3D BCC workload on 32^3 (the 64^3 box at half resolution keeps the test short):
+    # the mixed path (float inner iterations) reaches the FP64 path's energy to 1e-8
+    w = inputs.config_3d_bcc(32)
+    p = olb.Problem.from_workload(w)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        ctx = _ctx(lbtr, w, lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED)
+        phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+        o = lbtr.default_tr_opts()
+        o.eps = 1e-8
+        o.max_outer = 300
+        o.sub.rel_tol = 1e-6
+        info = lbtr.lb_imex_tr_solve(ctx, phi, opts=o)
+        v = phi.cpu().numpy()
+        assert np.max(np.abs(olb.gradient(p, v))) < 1e-8
+        assert abs(info["energy"] - olb.energy(p, v)) < 1e-12
+        out[prec] = info
+    assert abs(out["mixed"]["energy"] - out["fp64"]["energy"]) < 1e-8
+    assert (out["mixed"]["lambda_min"] >= -1e-8) == (out["fp64"]["lambda_min"] >= -1e-8)
