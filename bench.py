@@ -256,9 +256,20 @@ def time_tr(lbtr, w, prec: str, outer: int) -> dict:
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     n_out = max(1, info["outer"])
-    return {"outer_iters": n_out, "seconds": dt, "tr_iters_per_s": n_out / dt,
-            "inner_iters": info["inner"], "inner_iters_per_s": info["inner"] / dt,
-            "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6}
+    out = {"outer_iters": n_out, "seconds": dt, "tr_iters_per_s": n_out / dt,
+           "inner_iters": info["inner"], "inner_iters_per_s": info["inner"] / dt,
+           "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6}
+    # per-kernel-class breakdown of one more outer iteration (CUDA events per launch)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
+    o.max_outer = 1
+    lbtr.lb_profile_enable(ctx, True)
+    info1 = lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    prof = lbtr.lb_profile_read(ctx)
+    lbtr.lb_profile_enable(ctx, False)
+    n1 = max(1, info1["inner"])
+    out["profiled_outer_iteration"] = {"inner_iters": n1, "classes": {
+        k: {"total_ms": v[0], "launches": v[1], "us_per_inner_iter": 1e3 * v[0] / n1} for k, v in prof.items() if v[1] > 0}}
+    return out
 
 
 def main():
@@ -274,6 +285,8 @@ def main():
                     help="time only the mixed HVP at --size (small runs for profilers)")
     ap.add_argument("--pool", type=int, default=0, help="override the number of (phi, v, Hv) triples")
     ap.add_argument("--tr-outer", type=int, default=4, help="outer IMEX-TR iterations timed per precision")
+    ap.add_argument("--profile-sub", type=int, default=0,
+                    help="profile this many IMEX inner iterations per precision and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -303,6 +316,36 @@ def main():
     dt = max_over_ranks(dt, world)
     hvps = args.batch * args.steps * world
     value = hvps / dt
+
+    if args.profile_sub > 0:
+        # per-kernel-class times of a fixed number of IMEX inner iterations (Algorithm 3)
+        res = {}
+        for prec in ("mixed", "fp64"):
+            c = ctx if prec == "mixed" else lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
+                                                                          lbtr.LB_FP64)
+            dt_ = torch.float32 if prec == "mixed" else torch.float64
+            phi_t = torch.tensor(w.phi0, dtype=dt_, device=dev)
+            g_t = torch.empty_like(phi_t)
+            lbtr.lb_energy_grad(c, phi_t, g_t)
+            d_t = torch.empty_like(phi_t)
+            o = lbtr.default_sub_opts()
+            o.eps_sub = 0.0
+            o.rel_tol = 0.0
+            o.max_iter = args.profile_sub
+            o.check_every = args.profile_sub
+            lbtr.lb_tr_subproblem(c, phi_t, g_t, 1.0, d_t, opts=o, raise_on_noconv=False)
+            lbtr.lb_profile_enable(c, True)
+            t0 = time.perf_counter()
+            info = lbtr.lb_tr_subproblem(c, phi_t, g_t, 1.0, d_t, opts=o, raise_on_noconv=False)
+            wall = time.perf_counter() - t0
+            prof = lbtr.lb_profile_read(c)
+            lbtr.lb_profile_enable(c, False)
+            n1 = max(1, info["iterations"])
+            res[prec] = {"iterations": n1, "wall_us_per_iter": 1e6 * wall / n1,
+                         "classes": {k: {"launches": v[1], "us_per_iter": 1e3 * v[0] / n1}
+                                     for k, v in prof.items() if v[1] > 0}}
+        print(json.dumps({"mode": "profile-sub", "size": M, **res}), flush=True)
+        return
 
     if args.only_hvp:
         if rank == 0:

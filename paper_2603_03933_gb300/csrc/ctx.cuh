@@ -1,5 +1,6 @@
 // The lb_ctx object behind the C ABI and its host-side drivers.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -129,9 +130,12 @@ struct lb_ctx {
         if ((st = launch_status("lb_tr_subproblem/init"))) return st;
         lbtr::ImexState hs;
         int j = 1;
+        int chunk = 2;     // chunks grow 2, 4, 8, ... up to check_every: little work is wasted
+                           // on no-op launches after an early convergence
         while (true) {
-            int cnt = o.check_every;
+            int cnt = std::min(chunk, std::max(2, o.check_every));
             if (cnt % 2) ++cnt;
+            chunk = std::min(2 * chunk, std::max(2, o.check_every));
             p.imex_iterate(phi, g, j, cnt, s);
             j += cnt;
             if ((st = launch_status("lb_tr_subproblem/iterate"))) return st;

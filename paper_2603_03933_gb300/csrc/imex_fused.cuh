@@ -1,0 +1,259 @@
+// One IMEX iteration's reciprocal-space work in a single cooperative kernel.
+//
+// The CTAs of a cooperative grid own fixed tiles of columns of the innermost axis
+// (z in 3D, y in 2D) and keep them in shared memory across grid barriers:
+//   1. forward transform of b_j's columns, k = 0 removed; b_j stored for the next
+//      residual; ||b_{j-1} - b_j||^2 / eta^2 (the Algorithm 3 residual of d_j, by the
+//      identity g + (H + lambda_j I) d_j = (b_{j-1} - b_j) / eta) and the secular sums
+//      at lambda = 0 and at the previous multiplier are reduced over the grid;
+//   2. the convergence test of Algorithm 3; then the multiplier rule of
+//      eq. lambda_update_rule (Newton on phi(lambda) = r^2), each Newton step a sum over
+//      the register-resident terms c_i = w_i |b_i|^2 / N^2 and a_i = 1 + eta Lambda_i;
+//   3. d_{j+1} = b_j / (1 + eta (Lambda + lambda_{j+1})) (eq. imex-scheme) in place and the
+//      inverse transform of the columns, written for the next x/y pass.
+// Each spectrum element is read from and written to HBM once per iteration here,
+// instead of three separate passes plus a re-read per Newton step.
+#pragma once
+#include "aux_kernels.cuh"
+#include "passes.cuh"
+
+namespace lbtr {
+
+template <typename T> struct ZfArgs {
+    cplx<T>* work;            // in: b_j after the outer transforms; out: d_{j+1} after the inner inverse
+    const cplx<T>* bold;      // b_{j-1} (fully transformed)
+    cplx<T>* bnew;            // b_j (fully transformed) is written here
+    const cplx<T>* tw;
+    const T* qtab;
+    ColSeg seg[2];
+    int nb_main;              // main-segment tiles
+    int ntiles;               // all tiles
+    int dim, m;
+    ImexState* st;
+    double* partials;         // [2][NQ][gridDim]
+    GridBar bar;
+    T xi2, eta;
+    double inv_n, inv_n2;
+    double r, rtol, steptol, eps_abs, eps_rel_abs;
+    int check, max_iter;
+    long long spec_half;      // rows * H: offset of nyq within a spectrum
+};
+
+__host__ __device__ constexpr int zf_nt(int m, int tpc) { return 2 * m * tpc > 1024 ? 1024 : 2 * m * tpc; }
+template <typename T> __host__ __device__ constexpr size_t zf_smem(int m, int tpc) {
+    return sizeof(cplx<T>) * ((size_t)m + (size_t)m * (16 * tpc + 1)) + 3 * (size_t)m * sizeof(T) + 256 * sizeof(double);
+}
+
+template <typename T, int M, int TPC>
+__global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
+    constexpr int NL = 16 * TPC, NT = zf_nt(M, TPC), LD = NL + 1, H = M / 2;
+    constexpr int ESTEP = NT / NL, IT = M / ESTEP;
+    constexpr int HSH = (H >= 256) ? 8 : (H >= 128) ? 7 : (H >= 64) ? 6 : (H >= 32) ? 5 : (H >= 16) ? 4 : (H >= 8) ? 3 : 2;
+    static_assert(NT % NL == 0 && M % ESTEP == 0, "tile mapping");
+    using C = cplx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + M;
+    T* qt = reinterpret_cast<T*>(buf + M * LD);
+    double* red = reinterpret_cast<double*>(qt + 3 * M);
+    ImexState* st = a.st;
+    if (*(volatile int*)&st->done) return;
+    const C zero = mk<T>((T)0, (T)0);
+
+    // this thread's line: tile q of the CTA, line l within the tile
+    const int Lloc = threadIdx.x % NL;
+    const int e0 = threadIdx.x / NL;
+    const int q = Lloc / 16, l = Lloc % 16;
+    const int gt = blockIdx.x * TPC + q;
+    const int segi = gt < a.nb_main ? 0 : 1;
+    const ColSeg s = a.seg[segi];
+    const int l0 = (segi == 0 ? gt : gt - a.nb_main) * 16;
+    const bool ok = gt < a.ntiles && (l0 + l) < s.nlines;
+    const long long lmask = (1LL << s.lg_shift) - 1;
+    const int Lg = l0 + l;
+    const long long base = ok ? (long long)(Lg >> s.lg_shift) * s.lhi + (long long)(Lg & lmask) * s.llo : 0;
+    const long long soff = segi == 0 ? 0 : a.spec_half;
+
+    // 1. loads: b_j columns (work) and b_{j-1} (bold), all issued up front
+    C v[IT], old[IT];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int e = e0 + t * ESTEP;
+        const long long ad = soff + base + (long long)e * s.es;
+        v[t] = ok ? a.work[ad] : zero;
+        old[t] = (ok && a.check) ? a.bold[ad] : zero;
+    }
+    for (int i = threadIdx.x; i < M; i += NT) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < 3 * M; i += NT) qt[i] = a.qtab[i];
+#pragma unroll
+    for (int t = 0; t < IT; ++t) buf[(e0 + t * ESTEP) * LD + Lloc] = v[t];
+    __syncthreads();
+    fft_lines<T, -1, M, NL, NT>(buf, tw, M);
+
+    // 2. residual, secular terms, store b_j
+    const T eta = a.eta, n2 = (T)a.inv_n2;
+    const double lam_prev = st->lam;
+    const int j = st->it + 1;
+    T cc[IT], aa[IT];
+    Acc<T> acc[5];
+    const T elp = (T)(a.eta * lam_prev);
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int e = e0 + t * ESTEP;
+        C x = buf[e * LD + Lloc];
+        const int kx = s.kx_const >= 0 ? s.kx_const : (Lg & (H - 1));
+        T by, bz;
+        bool zo;
+        if (a.dim == 3) {
+            const int y = s.kx_const >= 0 ? Lg : (Lg >> HSH);
+            by = qt[M + y];
+            bz = qt[2 * M + e];
+            zo = (y == 0);
+        } else {
+            by = qt[M + e];
+            bz = (T)0;
+            zo = true;
+        }
+        const T wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
+        const bool is0 = (s.kx_const < 0) && kx == 0 && zo && e == 0;
+        if (is0 || !ok) x = zero;
+        buf[e * LD + Lloc] = x;
+        const T tt = (T)1 - (qt[kx] + by + bz);
+        const T ai = (T)1 + eta * a.xi2 * tt * tt;
+        const T ci = ok ? wgt * (x.x * x.x + x.y * x.y) * n2 : (T)0;
+        cc[t] = ci;
+        aa[t] = ai;
+        if (ok) {
+            const T dx = old[t].x - x.x, dy = old[t].y - x.y;
+            acc[0].add(wgt * (dx * dx + dy * dy));
+            acc[1].add(wgt * (x.x * x.x + x.y * x.y));
+            const T den = ai + elp;
+            const T qv = ci / (den * den);
+            acc[2].add(ci / (ai * ai));
+            acc[3].add(qv);
+            acc[4].add((T)-2 * eta * qv / den);
+            a.bnew[soff + base + (long long)e * s.es] = x;
+        }
+    }
+    double tot[5];
+    block_sum<T, 5>(acc, red, tot);
+    double* P = a.partials;
+    const int G = gridDim.x;
+    int stepi = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) P[(stepi & 1) * 5 * G + k * G + blockIdx.x] = tot[k];
+    if (!grid_sync(a.bar)) return;
+    double sums[5];
+    {
+        __shared__ double sh[5];
+        if (threadIdx.x < 32) {
+            for (int k = 0; k < 5; ++k) {
+                double x = 0.0;
+                for (int b = threadIdx.x; b < G; b += 32) x += ((volatile double*)P)[(stepi & 1) * 5 * G + k * G + b];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+                if (threadIdx.x == 0) sh[k] = x;
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < 5; ++k) sums[k] = sh[k] * (k < 2 ? a.inv_n2 : 1.0);
+        __syncthreads();
+    }
+    ++stepi;
+
+    // convergence of d_j (skipped on the initial call, which only sets up lambda_1)
+    if (a.check) {
+        const double res = sqrt(fmax(sums[0], 0.0)) / a.eta;
+        const bool bad = !isfinite(res) || !isfinite(sums[1]);
+        const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+        if (bad || conv || j >= a.max_iter) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->residual = res;
+                st->bnorm2 = sums[1];
+                st->final_lam = lam_prev;
+                st->final_src = (j - 1) & 1;
+                st->it = j;
+                st->done = bad ? 3 : (conv ? 1 : 2);
+            }
+            return;
+        }
+    }
+
+    // the multiplier rule: 0 if phi(0) <= r^2, else Newton from the previous multiplier
+    const double r2 = a.r * a.r;
+    double lam = 0.0;
+    long long newton = 0;
+    if (!(sums[2] <= r2)) {
+        lam = lam_prev;
+        double phi = lam_prev == 0.0 ? sums[2] : sums[3], dphi = sums[4];
+        for (int it = 0; it < 60; ++it) {
+            if (fabs(phi - r2) <= a.rtol * r2) break;
+            double ln = lam - (phi - r2) / dphi;
+            if (!(ln > 0.0)) ln = 0.0;
+            ++newton;
+            const bool small = fabs(ln - lam) <= a.steptol * (1.0 + ln);
+            lam = ln;
+            if (small) break;
+            const T el = (T)(a.eta * lam);
+            Acc<T> ac2[2];
+#pragma unroll
+            for (int t = 0; t < IT; ++t) {
+                const T den = aa[t] + el;
+                const T qv = cc[t] / (den * den);
+                ac2[0].add(qv);
+                ac2[1].add((T)-2 * eta * qv / den);
+            }
+            double t2[2];
+            block_sum<T, 2>(ac2, red, t2);
+            if (threadIdx.x == 0) {
+                P[(stepi & 1) * 5 * G + 0 * G + blockIdx.x] = t2[0];
+                P[(stepi & 1) * 5 * G + 1 * G + blockIdx.x] = t2[1];
+            }
+            if (!grid_sync(a.bar)) return;
+            __shared__ double sh2[2];
+            if (threadIdx.x < 32) {
+                for (int k = 0; k < 2; ++k) {
+                    double x = 0.0;
+                    for (int b = threadIdx.x; b < G; b += 32) x += ((volatile double*)P)[(stepi & 1) * 5 * G + k * G + b];
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+                    if (threadIdx.x == 0) sh2[k] = x;
+                }
+            }
+            __syncthreads();
+            phi = sh2[0];
+            dphi = sh2[1];
+            __syncthreads();
+            ++stepi;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->lam = lam;
+        st->newton += newton;
+        if (a.check) {
+            st->it = j;
+            st->residual = sqrt(fmax(sums[0], 0.0)) / a.eta;
+            st->bnorm2 = sums[1];
+        }
+    }
+
+    // 3. the implicit diagonal solve and the inverse transform of the columns
+    const T el = (T)(a.eta * lam);
+    const T ks = (T)a.inv_n;
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int e = e0 + t * ESTEP;
+        C x = buf[e * LD + Lloc];
+        const T f = ks / (aa[t] + el);
+        buf[e * LD + Lloc] = mk<T>(x.x * f, x.y * f);
+    }
+    __syncthreads();
+    fft_lines<T, +1, M, NL, NT>(buf, tw, M);
+#pragma unroll
+    for (int t = 0; t < IT; ++t) {
+        const int e = e0 + t * ESTEP;
+        if (ok) a.work[soff + base + (long long)e * s.es] = buf[e * LD + Lloc];
+    }
+}
+
+}  // namespace lbtr

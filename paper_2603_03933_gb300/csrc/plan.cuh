@@ -119,6 +119,7 @@ private:
     void mid_outer(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done = nullptr);
     RedSlot redslot(int slot, int nq, unsigned max_mask);
     void secular(const C* b, int check, int j, cudaStream_t s);
+    void zfused(const C* bold, C* bnew, int check, cudaStream_t s);
 
     int dim_ = 0, m_ = 0, h_ = 0, rows_ = 0;
     long long n_ = 0;
@@ -150,6 +151,8 @@ private:
     cudaError_t launch_err_ = cudaSuccess;
     Prof* prof_ = nullptr;
     bool use_planes_ = false;
+    int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
+    size_t zf_smem_ = 0;
     double fb() const { return (double)n_ * sizeof(T); }
     double sb() const { return (double)spec_len() * sizeof(C); }
 };

@@ -5,6 +5,7 @@
 
 #include "plan.cuh"
 #include "planes.cuh"
+#include "imex_fused.cuh"
 
 namespace lbtr {
 
@@ -70,6 +71,11 @@ template <typename T, int M> cudaError_t set_plane_attrs() {
     return e;
 }
 
+template <typename T, int M, int TPC> const void* zf_kernel() {
+    if constexpr (M >= 16) return (const void*)k_imex_zfused<T, M, TPC>;
+    return nullptr;
+}
+
 template <typename T, int M> cudaError_t set_smem_attrs() {
     cudaError_t e = cudaSuccess;
     auto setx = [&](const void* f) {
@@ -132,6 +138,31 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     coop_blocks_ = nsm * occ;
     if (coop_blocks_ > 4 * nsm) coop_blocks_ = 4 * nsm;
 
+    // fused reciprocal-space IMEX kernel: smallest tiles-per-CTA whose cooperative grid
+    // fits on the device with the columns resident in shared memory
+    {
+        const int nb_main_i = (int)(((long long)(dim_ == 3 ? m_ * h_ : h_) + COL_NL - 1) / COL_NL);
+        const int nb_nyq_i = ((dim_ == 3 ? m_ : 1) + COL_NL - 1) / COL_NL;
+        zf_ntiles_ = nb_main_i + nb_nyq_i;
+        zf_nbmain_ = nb_main_i;
+        zf_tpc_ = 0;
+        for (int tpc = 1; tpc <= 4 && m_ >= 16; tpc *= 2) {
+            const size_t sm = sizeof(T) == 8 ? zf_smem<double>(m_, tpc) : zf_smem<float>(m_, tpc);
+            if (sm > 227 * 1024) break;
+            const void* f = nullptr;
+            LB_SWITCH_M(m_, {
+                if (tpc == 1) f = zf_kernel<T, M, 1>();
+                else if (tpc == 2) f = zf_kernel<T, M, 2>();
+                else f = zf_kernel<T, M, 4>();
+            });
+            if (!f) break;
+            LB_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int per = 0;
+            LB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, zf_nt(m_, tpc), sm));
+            const int grid = (zf_ntiles_ + tpc - 1) / tpc;
+            if (per >= 1 && grid <= per * nsm) { zf_tpc_ = tpc; zf_grid_ = grid; zf_smem_ = sm; break; }
+        }
+    }
     int gx = (rows_ + x_nl(m_) - 1) / x_nl(m_);
     int gc = (int)((((long long)rows_ * h_) + COL_NL - 1) / COL_NL + (rows_ + COL_NL - 1) / COL_NL);
     max_blocks_ = std::max(std::max(gx, gc), std::max(coop_blocks_, 8 * nsm));
@@ -148,7 +179,7 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     size_t o_p = take(sizeof(double) * S_COUNT * SLOT_Q * (size_t)max_blocks_);
     size_t o_r = take(sizeof(double) * S_COUNT * SLOT_Q);
     size_t o_t = take(sizeof(unsigned) * S_COUNT);
-    size_t o_sp = take(sizeof(double) * 2 * 3 * (size_t)coop_blocks_);
+    size_t o_sp = take(sizeof(double) * 2 * 5 * (size_t)std::max(coop_blocks_, zf_grid_));
     size_t o_bar = take(sizeof(unsigned) * 2);
     size_t o_err = take(sizeof(int));
     size_t o_st = take(sizeof(ImexState));
@@ -458,6 +489,42 @@ template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaSt
     if (prof_) prof_->end(K_SECULAR, e0, s, sb());
 }
 
+template <typename T> void Plan<T>::zfused(const C* bold, C* bnew, int check, cudaStream_t s) {
+    ZfArgs<T> a;
+    a.work = d_work_; a.bold = bold; a.bnew = bnew;
+    a.tw = d_tw_; a.qtab = d_qtab_;
+    const long long M = m_, H = h_;
+    auto lg = [](long long v) { int k = 0; while ((1LL << k) < v) ++k; return k; };
+    if (dim_ == 3) {
+        a.seg[0] = ColSeg{(int)(M * H), lg(M * H), 0, 1, M * H, 0, -1};
+        a.seg[1] = ColSeg{(int)M, lg(M), 0, 1, M, 0, (int)H};
+    } else {
+        a.seg[0] = ColSeg{(int)H, lg(H), 0, 1, H, 0, -1};
+        a.seg[1] = ColSeg{1, 0, 0, 0, 1, 1, (int)H};
+    }
+    a.nb_main = zf_nbmain_; a.ntiles = zf_ntiles_;
+    a.dim = dim_; a.m = m_;
+    a.st = d_state_;
+    a.partials = d_secpart_;
+    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 1; a.bar.err = d_err_; a.bar.budget = budget_;
+    a.xi2 = (T)xi2_; a.eta = (T)eta;
+    a.inv_n = 1.0 / (double)n_; a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
+    a.r = r_; a.rtol = rtol_; a.steptol = steptol_; a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_;
+    a.check = check; a.max_iter = max_iter_;
+    a.spec_half = (long long)rows_ * h_;
+    void* args[] = {&a};
+    const void* f = nullptr;
+    LB_SWITCH_M(m_, {
+        if (zf_tpc_ == 1) f = zf_kernel<T, M, 1>();
+        else if (zf_tpc_ == 2) f = zf_kernel<T, M, 2>();
+        else f = zf_kernel<T, M, 4>();
+    });
+    cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+    cudaError_t e = cudaLaunchCooperativeKernel(f, dim3(zf_grid_), dim3(zf_nt(m_, zf_tpc_)), args, zf_smem_, s);
+    if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+    if (prof_) prof_->end(K_COLI, e0, s, 4 * sb());
+}
+
 template <typename T>
 int Plan<T>::imex_init(const T* phi, const T* g, const T* d0, const double* dscale_dev, double r,
                        double eps_abs, double eps_rel_abs, int max_iter, cudaStream_t s) {
@@ -469,6 +536,10 @@ int Plan<T>::imex_init(const T* phi, const T* g, const T* d0, const double* dsca
     cudaMemsetAsync(d_state_, 0, sizeof(ImexState), s);
     cudaMemsetAsync(d_b_[1], 0, sizeof(C) * spec_len(), s);
     fwd_outer(XF_IMEX0, nullptr, phi, g, d0, dscale_dev, d_work_, S_RED0, s);
+    if (zf_tpc_ > 0) {
+        zfused(d_b_[1], d_b_[0], 0, s);
+        return 0;
+    }
     const double inv_n = 1.0 / (double)n_;
     cols(inner, C_IMEX_OUT, d_work_, d_b_[0], d_b_[1], (T)1, inv_n * inv_n, 0.0, nullptr, S_IMEX, s);
     secular(d_b_[0], 0, 0, s);
@@ -479,6 +550,15 @@ template <typename T> int Plan<T>::imex_iterate(const T* phi, const T* g, int j0
     const int inner = dim_ == 3 ? 2 : 1;
     const double inv_n = 1.0 / (double)n_;
     const int* done = &d_state_->done;
+    if (zf_tpc_ > 0) {
+        // d_work_ holds d_j after the inner inverse; x/y pass builds b_j; the fused kernel
+        // does the rest of the iteration
+        for (int j = j0; j < j0 + count; ++j) {
+            mid_outer(XM_IMEX, d_work_, phi, g, (T)1, s, done);
+            zfused(d_b_[(j - 1) & 1], d_b_[j & 1], 1, s);
+        }
+        return 0;
+    }
     for (int j = j0; j < j0 + count; ++j) {
         C* src = d_b_[(j - 1) & 1];
         C* dst = d_b_[j & 1];

@@ -1,6 +1,8 @@
 // Outer IMEX-TR loop (Algorithms 1 and 2 of the paper) and the Lanczos lambda_min driver.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <vector>
@@ -279,6 +281,8 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
     P.eta = o.sub.eta;
     if (p32) p32->eta = o.sub.eta;
     info->lambda_min = std::numeric_limits<double>::quiet_NaN();
+    const char* tr_env = std::getenv("LBTR_TRACE");
+    const bool trace = tr_env && tr_env[0] == '1';   // one JSON line per outer iteration on stderr
     lb_status result = LB_ERR_NOCONV;
     int j = 0;
     double E = 0.0, gmax = 0.0;
@@ -405,6 +409,13 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
         }
         S.rho_prev = rho;
         S.have_rho = true;
+        if (trace)
+            std::fprintf(stderr,
+                         "{\"j\": %d, \"E\": %.15g, \"gmax\": %.3e, \"r\": %.6g, \"nu\": %.6g, \"mu\": %.6g, "
+                         "\"lambda\": %.6g, \"snorm\": %.6g, \"rho\": %.6g, \"inner\": %d, \"sub_status\": %d, "
+                         "\"acc\": %d, \"con\": %d, \"shr\": %d}\n",
+                         j, E, gmax, S.r, S.nu, S.mu, lam, sn, rho, si.iterations, (int)ss, info->accepted,
+                         info->contracted, info->shrunk);
     }
     info->outer = j;
     if (result != LB_OK) {
