@@ -214,6 +214,25 @@ void lb_default_tr_opts(lb_tr_opts *o);
 lb_status lb_imex_tr_solve(lb_ctx *ctx, double *phi_inout, const lb_tr_opts *opts,
                            lb_tr_info *info, lb_stream stream);
 
+/*
+ * Hessian-vector product that allocates nothing (no counterpart in the paper; an
+ * interface for callers that cannot call cudaMalloc, e.g. plug-ins whose host
+ * framework owns all device memory, or loops that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree).  Same operator as lb_hessvec, without a
+ * context: the problem is passed directly and the scratch is a fixed 3 MiB device
+ * array inside the library, held on every device that loads it until the process
+ * exits.  Limits: N = n^dim <= 2^18 points (up to 64^3 or 512^2); larger grids return
+ * LB_ERR_UNSUPPORTED.  Fields are double for LB_FP64 and float for LB_MIXED.
+ * The first call on each device resolves the scratch address and sets kernel
+ * attributes (once per device, with that device current); make that first call
+ * before any stream capture.  Every call shares the one scratch array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Asynchronous on `stream` apart from two small host-to-device table
+ * copies.
+ */
+lb_status lb_hessvec_noalloc(const lb_problem *prob, lb_precision prec, const void *phi, const void *v,
+                             void *hv, lb_stream stream);
+
 /* Profiling aid.  Kernel classes of the library's launches: */
 typedef enum {
     LB_K_XFWD = 0,     /* forward x-row real transform with its pointwise preprocessing */

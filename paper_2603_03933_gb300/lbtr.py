@@ -92,6 +92,7 @@ SIGNATURES = [
     ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
+    ("lb_hessvec_noalloc", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, _VP, _VP, _VP, _VP]),
 ]
 KERNEL_CLASSES = ["xfwd", "xinv", "xmid", "col_y", "col_inner", "secular", "reduce"]
 
@@ -312,3 +313,24 @@ def lb_profile_read(ctx: Context) -> dict:
                "lb_profile_read")
         out[name] = (ms.value, n.value, b.value)
     return out
+
+
+def lb_hessvec_noalloc(dim: int, n: int, box, xi: float, tau: float, gamma: float, precision: int,
+                       phi, v, hv, stream=None):
+    """hv = H v without a context or any device allocation (C: lb_hessvec_noalloc).
+
+    For callers that cannot allocate device memory.  box: (L_x, L_y[, L_z]).  Scratch is a
+    fixed array inside the library (N <= 2^18 points); concurrent calls race."""
+    torch = _torch()
+    want = torch.float64 if precision == LB_FP64 else torch.float32
+    npts = n ** dim
+    for name, t in (("phi", phi), ("v", v), ("hv", hv)):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != want or t.numel() != npts:
+            raise ValueError(f"{name} must be a contiguous CUDA {want} tensor of {npts} elements")
+    box = list(box) + [1.0] * (3 - len(box))
+    prob = lb_problem(dim, n, (ctypes.c_double * 3)(*box[:3]), xi, tau, gamma)
+    st = load().lb_hessvec_noalloc(ctypes.byref(prob), precision, ctypes.c_void_p(phi.data_ptr()),
+                                   ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(hv.data_ptr()), _stream(stream))
+    if st != 0:
+        raise LBError(st, "lb_hessvec_noalloc")
+    return hv
