@@ -35,7 +35,12 @@ L2_BYTES = 129 * 1024 * 1024
 
 # ncu DRAM traffic per launch of a kernel class, with the hash of the CUDA sources it
 # was captured from (a traffic figure is reported only while the sources match).
-TRAFFIC = {}
+TRAFFIC = {
+    # k_plane_fwd<float,128,XF_HVPMEAN>, k_cols<float,128,C_LAM>, k_plane_inv<float,128,XI_HVP>
+    "xfwd": (16817920, "6bf0cb0e8b6ae985"),
+    "col_inner": (8546304, "6bf0cb0e8b6ae985"),
+    "xinv": (25317888, "6bf0cb0e8b6ae985"),
+}
 
 
 def csrc_hash() -> str:
