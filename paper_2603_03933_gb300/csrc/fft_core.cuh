@@ -55,10 +55,48 @@ template <int SIGN, typename T> __device__ __forceinline__ void dft8(cplx<T>* u)
     for (int m = 0; m < 4; ++m) { u[2 * m] = a[m]; u[2 * m + 1] = b[m]; }
 }
 
+// x * (c + i s)
+template <typename T> __device__ __forceinline__ cplx<T> crot(cplx<T> x, T c, T s) {
+    return mk<T>(x.x * c - x.y * s, x.x * s + x.y * c);
+}
+
+// 16 points as 4 x 4: n = n1 + 4 n2, k = k2 + 4 k1; length-4 DFTs over n2, the twiddle
+// exp(SIGN 2 pi i n1 k2 / 16), length-4 DFTs over n1.  Output in natural order.
+template <int SIGN, typename T> __device__ __forceinline__ void dft16(cplx<T>* u) {
+    using C = cplx<T>;
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;   // cos, sin of pi/8
+    const T h = (T)0.70710678118654752440, sg = (T)SIGN;
+    C v[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        C t[4] = {u[n1], u[n1 + 4], u[n1 + 8], u[n1 + 12]};
+        dft4<SIGN>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[n1][k2] = t[k2];
+    }
+    v[1][1] = crot(v[1][1], c1, sg * s1);     // angle 1 * 2 pi / 16
+    v[1][2] = crot(v[1][2], h, sg * h);       // 2
+    v[1][3] = crot(v[1][3], s1, sg * c1);     // 3
+    v[2][1] = crot(v[2][1], h, sg * h);       // 2
+    v[2][2] = cmul_i<SIGN>(v[2][2]);          // 4
+    v[2][3] = crot(v[2][3], -h, sg * h);      // 6
+    v[3][1] = crot(v[3][1], s1, sg * c1);     // 3
+    v[3][2] = crot(v[3][2], -h, sg * h);      // 6
+    v[3][3] = crot(v[3][3], -c1, -sg * s1);   // 9
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        C t[4] = {v[0][k2], v[1][k2], v[2][k2], v[3][k2]};
+        dft4<SIGN>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) u[k2 + 4 * k1] = t[k1];
+    }
+}
+
 template <int SIGN, int R, typename T> __device__ __forceinline__ void dft_r(cplx<T>* u) {
     if (R == 2) dft2<SIGN>(u[0], u[1]);
     else if (R == 4) dft4<SIGN>(u);
-    else dft8<SIGN, T>(u);
+    else if (R == 8) dft8<SIGN, T>(u);
+    else dft16<SIGN, T>(u);
 }
 
 // ---- radix plan: 8s first, then 4/2; 16 is done as 4*4 ---------------------------

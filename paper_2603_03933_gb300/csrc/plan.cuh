@@ -151,6 +151,7 @@ private:
     cudaError_t launch_err_ = cudaSuccess;
     Prof* prof_ = nullptr;
     bool use_planes_ = false;
+    int ln_grid_cap_ = 0;     // persistent grid of the pipelined column passes (0: not used)
     int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
     size_t zf_smem_ = 0;
     double fb() const { return (double)n_ * sizeof(T); }

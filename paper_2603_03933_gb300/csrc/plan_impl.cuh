@@ -5,6 +5,7 @@
 
 #include "plan.cuh"
 #include "planes.cuh"
+#include "lines.cuh"
 #include "imex_fused.cuh"
 
 namespace lbtr {
@@ -49,6 +50,30 @@ template <typename T, int M, int MODE> void launch_pinv(const XiArgs<T>& a, cuda
 }
 template <typename T, int M, int MODE> void launch_pmid(const XmArgs<T>& a, cudaStream_t s) {
     if constexpr (M >= 32 && M <= 128) k_plane_mid<T, M, MODE><<<M, plane_nt(M), plane_smem<T>(M), s>>>(a);
+}
+
+template <typename T, int M, int MODE> void launch_lines(const ColArgs<T>& a, int ntiles, int grid, cudaStream_t s) {
+    if constexpr (M >= 16 && M <= 256 && ln_mode_ok(MODE)) k_lines<T, M, MODE><<<grid, ln_nt(M), ln_smem<T>(M), s>>>(a, ntiles);
+}
+
+// Shared-memory attributes of the pipelined column passes; *per = CTAs per SM of the C_LAM pass.
+template <typename T, int M> cudaError_t set_lines_attrs(int* per) {
+    cudaError_t e = cudaSuccess;
+    *per = 0;
+    if constexpr (M >= 16 && M <= 256) {
+        auto setl = [&](const void* f) {
+            cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ln_smem<T>(M));
+            if (r != cudaSuccess) e = r;
+        };
+        setl((const void*)k_lines<T, M, C_FWD>);
+        setl((const void*)k_lines<T, M, C_INV>);
+        setl((const void*)k_lines<T, M, C_LAM>);
+        setl((const void*)k_lines<T, M, C_LAM_E>);
+        setl((const void*)k_lines<T, M, C_SOLVE>);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_lines<T, M, C_LAM>, ln_nt(M), ln_smem<T>(M));
+    }
+    return e;
 }
 
 template <typename T, int M> cudaError_t set_plane_attrs() {
@@ -130,6 +155,13 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     if (use_planes_) {
         LB_SWITCH_M(m_, ea = set_plane_attrs<T, M>());
         if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+    }
+
+    {
+        int per = 0;
+        LB_SWITCH_M(m_, ea = set_lines_attrs<T, M>(&per));
+        if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+        ln_grid_cap_ = per > 0 ? nsm * per : 0;
     }
 
     int occ = 0;
@@ -327,7 +359,19 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : 1, 0u);
     a.done = done;
     cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
-    LB_SWITCH_M(m_, {
+    const bool lines = ln_grid_cap_ > 0 && ln_mode_ok(mode) && dst == nullptr && src == nullptr;
+    if (lines) {
+        const int lg_grid = std::min(grid, ln_grid_cap_);
+        LB_SWITCH_M(m_, {
+            switch (mode) {
+                case C_FWD: launch_lines<T, M, C_FWD>(a, grid, lg_grid, s); break;
+                case C_INV: launch_lines<T, M, C_INV>(a, grid, lg_grid, s); break;
+                case C_LAM: launch_lines<T, M, C_LAM>(a, grid, lg_grid, s); break;
+                case C_LAM_E: launch_lines<T, M, C_LAM_E>(a, grid, lg_grid, s); break;
+                default: launch_lines<T, M, C_SOLVE>(a, grid, lg_grid, s); break;
+            }
+        });
+    } else LB_SWITCH_M(m_, {
         switch (mode) {
             case C_FWD: launch_cols<T, M, C_FWD>(a, grid, s); break;
             case C_INV: launch_cols<T, M, C_INV>(a, grid, s); break;
