@@ -87,12 +87,24 @@ __device__ __forceinline__ void sum_partials(const double* p, int nq, double* ou
     __syncthreads();
 }
 
+// One Newton step towards the root of phi(lambda) = r^2 (eq. lambda_update_rule), taken on
+// the equivalent equation psi(lambda) = phi(lambda)^(-1/2) - 1/r = 0, which has the same
+// root.  For phi = sum_i c_i / (a_i + eta lambda)^2 with a_i > 0, psi is increasing and
+// concave (the secular-equation argument of More and Sorensen, 1983) and exactly linear
+// when one term dominates, so from the left the step never overshoots and from a warm
+// start near the root one or two steps reach the tolerance.  With psi' = -phi' phi^(-3/2) / 2
+// the step is lambda + 2 phi (1 - sqrt(phi) / r) / phi'; it is clamped at 0.
+__device__ __forceinline__ double secular_newton_step(double lam, double phi, double dphi, double r) {
+    double ln = lam + 2.0 * phi * (1.0 - sqrt(phi) / r) / dphi;
+    if (!isfinite(ln)) ln = lam - (phi - r * r) / dphi;
+    return ln > 0.0 ? ln : 0.0;
+}
+
 // Convergence check of the iterate d_j (residual identity g + (H + lam_j) d_j =
 // (b_{j-1} - b_j)/eta, which follows from eq. imex-scheme), then the lambda rule of
-// eq. lambda_update_rule for the next iterate: lam = 0 if phi(0) <= r^2, else Newton.
-// Newton starts from the previous multiplier (clamped at 0) instead of 0; it reaches
-// the same root because phi is convex and decreasing (a start right of the root
-// lands left of it after one step and then increases monotonically).
+// eq. lambda_update_rule for the next iterate: lam = 0 if phi(0) <= r^2, else Newton
+// (secular_newton_step) from the previous multiplier instead of 0; the root is the same,
+// phi being decreasing.
 template <typename T>
 __global__ void k_secular(SecArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -139,8 +151,7 @@ __global__ void k_secular(SecArgs<T> a) {
         if (lam_prev == 0.0) { phi = tot[0]; dphi = tot[2]; }
         for (int it = 0; it < 60; ++it) {
             if (fabs(phi - r2) <= a.rtol * r2) break;
-            double ln = lam - (phi - r2) / dphi;
-            if (!(ln > 0.0)) ln = 0.0;
+            const double ln = secular_newton_step(lam, phi, dphi, a.r);
             ++newton;
             bool small = fabs(ln - lam) <= a.steptol * (1.0 + ln);
             lam = ln;

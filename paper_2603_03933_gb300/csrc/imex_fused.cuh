@@ -16,6 +16,7 @@
 #pragma once
 #include "aux_kernels.cuh"
 #include "passes.cuh"
+#include "lines.cuh"
 
 namespace lbtr {
 
@@ -188,8 +189,7 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
         double phi = lam_prev == 0.0 ? sums[2] : sums[3], dphi = sums[4];
         for (int it = 0; it < 60; ++it) {
             if (fabs(phi - r2) <= a.rtol * r2) break;
-            double ln = lam - (phi - r2) / dphi;
-            if (!(ln > 0.0)) ln = 0.0;
+            const double ln = secular_newton_step(lam, phi, dphi, a.r);
             ++newton;
             const bool small = fabs(ln - lam) <= a.steptol * (1.0 + ln);
             lam = ln;
@@ -253,6 +253,282 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
     for (int t = 0; t < IT; ++t) {
         const int e = e0 + t * ESTEP;
         if (ok) a.work[soff + base + (long long)e * s.es] = buf[e * LD + Lloc];
+    }
+}
+
+
+// ---------------------------------------------------------------------------------
+// The same iteration with the columns held in registers as four-step line transforms
+// (the layout of k_lines): one cooperative grid of TPC tiles of LN_NL lines per CTA, every
+// tile of the spectrum resident at once.  Thread (l, i) of a tile keeps the L1 elements of
+// line l that the forward transform leaves with it, with their a = 1 + eta Lambda, across
+// the grid barriers of the multiplier rule (c = w |b|^2 / N^2 is recomputed from them).
+// The scalar part of each barrier step (the Algorithm 3 test, the Newton update of the
+// multiplier) runs in one thread per CTA and reaches the others through shared memory;
+// every CTA reads the same partial sums in the same order, so all take the same decision.
+// ---------------------------------------------------------------------------------
+__host__ __device__ constexpr int zl_nt(int m, int tpc) { return LN_NL * fs_l2(m) * tpc; }
+template <typename T> __host__ __device__ constexpr size_t zl_smem(int m, int tpc) {
+    return 2 * (size_t)tpc * LN_NL * (m + 1) * sizeof(cplx<T>) + 32 * 5 * sizeof(double);
+}
+
+// Newton update of the multiplier (secular_newton_step) with the stopping tests of the
+// rule; true if phi and phi' at the new lambda are needed for another step
+struct NewtonState {
+    double lam, r, r2, rtol, steptol;
+    long long newton;
+    int steps;
+};
+__device__ __forceinline__ bool newton_update(NewtonState& ns, double phi, double dphi) {
+    if (ns.steps >= 60) return false;
+    if (fabs(phi - ns.r2) <= ns.rtol * ns.r2) return false;
+    const double ln = secular_newton_step(ns.lam, phi, dphi, ns.r);
+    ++ns.newton;
+    ++ns.steps;
+    const bool small = fabs(ln - ns.lam) <= ns.steptol * (1.0 + ln);
+    ns.lam = ln;
+    return !small;
+}
+
+// sum the NQ per-CTA partials of barrier step `stepi` (warp 0) into sh[0..NQ); the loads
+// go to L2 (written by other CTAs before the barrier) and are independent, so they overlap
+template <int NQ>
+__device__ __forceinline__ void zl_gather(const double* P, int stepi, double* sh) {
+    const int G = gridDim.x;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            double x = 0.0;
+#pragma unroll 4
+            for (int b = threadIdx.x; b < G; b += 32) x += __ldcg(&P[(stepi & 1) * 5 * G + k * G + b]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            if (threadIdx.x == 0) sh[k] = x;
+        }
+    }
+}
+
+template <typename T, int M, int TPC>
+__global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(ZfArgs<T> a) {
+    constexpr int NL = LN_NL, L1 = fs_l1(M), L2 = fs_l2(M), RR = L1 / L2, TS = M + 1, H = M / 2;
+    constexpr int NTT = NL * L2;            // threads per tile
+    constexpr int HSH = (H >= 256) ? 8 : (H >= 128) ? 7 : (H >= 64) ? 6 : (H >= 32) ? 5 : (H >= 16) ? 4 : (H >= 8) ? 3 : 2;
+    static_assert((1 << HSH) == H, "H must be a power of two");
+    enum { ACT_RETURN = 0, ACT_EVAL = 1, ACT_SOLVE = 2 };
+    using C = cplx<T>;
+    ImexState* st = a.st;
+    if (*(volatile int*)&st->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int q = threadIdx.x / NTT, lt = threadIdx.x % NTT;
+    C* TA = reinterpret_cast<C*>(smem_raw) + (size_t)q * 2 * NL * TS;
+    C* TB = TA + NL * TS;
+    double* red = reinterpret_cast<double*>(reinterpret_cast<C*>(smem_raw) + (size_t)TPC * 2 * NL * TS);
+    __shared__ double s_sum[2];
+    __shared__ double s_lam;
+    __shared__ T s_el;
+    __shared__ int s_act;
+    __shared__ double sh[5];
+    __shared__ NewtonState ns;
+    const int l = lt % NL, i = lt / NL;
+    const C zero = mk<T>((T)0, (T)0);
+    const T* __restrict__ qt = a.qtab;
+
+    // this thread's line
+    const int tile = blockIdx.x * TPC + q;
+    const int segi = tile < a.nb_main ? 0 : 1;
+    const ColSeg& s = a.seg[segi];
+    const int L = (tile - (segi ? a.nb_main : 0)) * NL + l;
+    const bool ok = tile < a.ntiles && L < s.nlines;
+    const long long lmask = (1LL << s.lg_shift) - 1;
+    const long long base = (ok ? (long long)(L >> s.lg_shift) * s.lhi + (long long)(L & lmask) * s.llo : 0) +
+                           (segi ? a.spec_half : 0);
+    const long long es = s.es;
+    auto fo = [&](int m) { return i + L2 * (m / L2) + L1 * (m % L2); };   // element in slot m after the forward
+
+    // 1. b_j in the forward-input layout
+    C v[L1];
+#pragma unroll
+    for (int m = 0; m < L1; ++m) v[m] = ok ? a.work[base + (long long)(i + L2 * m) * es] : zero;
+
+    // 2. forward transform of the columns
+    dft_r<-1, L1, T>(v);
+#pragma unroll
+    for (int m = 1; m < L1; ++m) v[m] = cmul(v[m], __ldg(&a.tw[i * m]));
+#pragma unroll
+    for (int m = 0; m < L1; ++m) TA[l * TS + m * L2 + i] = v[m];
+    __syncthreads();
+    // b_{j-1} in the forward-output layout (in flight during the second half of the transform)
+    C old[L1];
+#pragma unroll
+    for (int m = 0; m < L1; ++m) old[m] = (ok && a.check) ? a.bold[base + (long long)fo(m) * es] : zero;
+#pragma unroll
+    for (int sb = 0; sb < RR; ++sb) {
+        const int aq = i + L2 * sb;
+#pragma unroll
+        for (int jj = 0; jj < L2; ++jj) v[sb * L2 + jj] = TA[l * TS + aq * L2 + jj];
+        dft_r<-1, L2, T>(&v[sb * L2]);
+    }
+
+    // 3. zero k = 0, store b_j, residual and secular sums
+    const int kx = s.kx_const >= 0 ? s.kx_const : (L & (H - 1));
+    T byz;
+    bool zo;
+    if (a.dim == 3) {
+        const int y = s.kx_const >= 0 ? L : (L >> HSH);
+        byz = qt[kx] + qt[M + y];
+        zo = (y == 0);
+    } else {
+        byz = qt[kx];
+        zo = true;
+    }
+    const T wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
+    const bool k0line = (s.kx_const < 0) && kx == 0 && zo;
+    const T* qe = qt + (a.dim == 3 ? 2 * M : M);
+    const T eta = a.eta, n2 = (T)a.inv_n2;
+    const double lam_prev = st->lam;
+    const int j = st->it + 1;
+    const T elp = (T)(a.eta * lam_prev);
+    T aa[L1];
+    const T cw = wgt * n2;
+    Acc<T> acc[5];
+#pragma unroll
+    for (int m = 0; m < L1; ++m) {
+        const int e = fo(m);
+        C x = v[m];
+        if (!ok || (k0line && e == 0)) x = zero;
+        v[m] = x;
+        const T tt = (T)1 - (byz + qe[e]);
+        const T ai = (T)1 + eta * a.xi2 * tt * tt;
+        const T ci = cw * (x.x * x.x + x.y * x.y);
+        aa[m] = ai;
+        if (ok) {
+            const T dx = old[m].x - x.x, dy = old[m].y - x.y;
+            acc[0].add(wgt * (dx * dx + dy * dy));
+            acc[1].add(wgt * (x.x * x.x + x.y * x.y));
+            const T den = ai + elp;
+            const T qv = ci / (den * den);
+            acc[2].add(ci / (ai * ai));
+            acc[3].add(qv);
+            acc[4].add((T)-2 * eta * qv / den);
+            a.bnew[base + (long long)e * es] = x;
+        }
+    }
+    double* P = a.partials;
+    const int G = gridDim.x;
+    int stepi = 0;
+    {
+        double tot[5];
+        block_sum<T, 5>(acc, red, tot);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 5; ++k) P[k * G + blockIdx.x] = tot[k];
+    }
+    if (!grid_sync(a.bar)) return;
+    zl_gather<5>(P, stepi, sh);
+    ++stepi;
+    if (threadIdx.x == 0) {
+        double sums[5];
+        for (int k = 0; k < 5; ++k) sums[k] = sh[k] * (k < 2 ? a.inv_n2 : 1.0);
+        int act = ACT_SOLVE;
+        // convergence of d_j (not on the initial call, which only sets up lambda_1)
+        if (a.check) {
+            const double res = sqrt(fmax(sums[0], 0.0)) / a.eta;
+            const bool bad = !isfinite(res) || !isfinite(sums[1]);
+            const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+            if (bad || conv || j >= a.max_iter) {
+                if (blockIdx.x == 0) {
+                    st->residual = res;
+                    st->bnorm2 = sums[1];
+                    st->final_lam = lam_prev;
+                    st->final_src = (j - 1) & 1;
+                    st->it = j;
+                    st->done = bad ? 3 : (conv ? 1 : 2);
+                }
+                act = ACT_RETURN;
+            }
+            s_sum[0] = res;
+            s_sum[1] = sums[1];
+        }
+        if (act != ACT_RETURN) {
+            // the multiplier rule: 0 if phi(0) <= r^2, else Newton from the previous multiplier
+            ns.r = a.r;
+            ns.r2 = a.r * a.r;
+            ns.rtol = a.rtol;
+            ns.steptol = a.steptol;
+            ns.newton = 0;
+            ns.steps = 0;
+            ns.lam = 0.0;
+            if (!(sums[2] <= ns.r2)) {
+                ns.lam = lam_prev;
+                if (newton_update(ns, lam_prev == 0.0 ? sums[2] : sums[3], sums[4])) act = ACT_EVAL;
+            }
+            s_lam = ns.lam;
+            s_el = (T)(a.eta * ns.lam);
+        }
+        s_act = act;
+    }
+    __syncthreads();
+    if (s_act == ACT_RETURN) return;
+    while (s_act == ACT_EVAL) {
+        const T el = s_el;
+        Acc<T> ac2[2];
+#pragma unroll
+        for (int m = 0; m < L1; ++m) {
+            const T den = aa[m] + el;
+            const T qv = cw * (v[m].x * v[m].x + v[m].y * v[m].y) / (den * den);
+            ac2[0].add(qv);
+            ac2[1].add((T)-2 * eta * qv / den);
+        }
+        double t2[2];
+        block_sum<T, 2>(ac2, red, t2);
+        if (threadIdx.x == 0) {
+            P[(stepi & 1) * 5 * G + 0 * G + blockIdx.x] = t2[0];
+            P[(stepi & 1) * 5 * G + 1 * G + blockIdx.x] = t2[1];
+        }
+        if (!grid_sync(a.bar)) return;
+        zl_gather<2>(P, stepi, sh);
+        ++stepi;
+        if (threadIdx.x == 0) {
+            const bool more = newton_update(ns, sh[0], sh[1]);
+            s_lam = ns.lam;
+            s_el = (T)(a.eta * ns.lam);
+            s_act = more ? ACT_EVAL : ACT_SOLVE;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->lam = s_lam;
+        st->newton += ns.newton;
+        if (a.check) {
+            st->it = j;
+            st->residual = s_sum[0];
+            st->bnorm2 = s_sum[1];
+        }
+    }
+
+    // 4. the implicit diagonal solve and the inverse transform of the columns
+    const T el = s_el;
+    const T ks = (T)a.inv_n;
+#pragma unroll
+    for (int m = 0; m < L1; ++m) {
+        const T f = ks / (aa[m] + el);
+        v[m] = mk<T>(v[m].x * f, v[m].y * f);
+    }
+#pragma unroll
+    for (int sb = 0; sb < RR; ++sb) {
+        const int aq = i + L2 * sb;
+        dft_r<+1, L2, T>(&v[sb * L2]);
+#pragma unroll
+        for (int c = 1; c < L2; ++c) v[sb * L2 + c] = cmul(v[sb * L2 + c], cconj(__ldg(&a.tw[c * aq])));
+#pragma unroll
+        for (int c = 0; c < L2; ++c) TB[l * TS + aq * L2 + c] = v[sb * L2 + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < L1; ++m) v[m] = TB[l * TS + m * L2 + i];
+    dft_r<+1, L1, T>(v);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < L1; ++m) a.work[base + (long long)(i + L2 * m) * es] = v[m];
     }
 }
 

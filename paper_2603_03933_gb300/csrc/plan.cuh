@@ -154,6 +154,7 @@ private:
     int ln_grid_cap_ = 0;     // persistent grid of the pipelined column passes (0: not used)
     int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
     size_t zf_smem_ = 0;
+    bool zf_lines_ = false;   // the fused iteration runs as k_imex_lines (else k_imex_zfused)
     double fb() const { return (double)n_ * sizeof(T); }
     double sb() const { return (double)spec_len() * sizeof(C); }
 };

@@ -96,6 +96,11 @@ template <typename T, int M> cudaError_t set_plane_attrs() {
     return e;
 }
 
+template <typename T, int M, int TPC> const void* zl_kernel() {
+    if constexpr (M >= 16 && M <= 256) return (const void*)k_imex_lines<T, M, TPC>;
+    return nullptr;
+}
+
 template <typename T, int M, int TPC> const void* zf_kernel() {
     if constexpr (M >= 16) return (const void*)k_imex_zfused<T, M, TPC>;
     return nullptr;
@@ -178,7 +183,32 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
         zf_ntiles_ = nb_main_i + nb_nyq_i;
         zf_nbmain_ = nb_main_i;
         zf_tpc_ = 0;
-        for (int tpc = 1; tpc <= 4 && m_ >= 16; tpc *= 2) {
+        zf_lines_ = false;
+        // register-resident columns, every tile on the device at once: the first of
+        // 1, 2, 4 tiles per CTA whose cooperative grid fits without spilling registers
+        for (int tpc = 1; tpc <= 4 && m_ >= 16 && m_ <= 256; tpc *= 2) {
+            const size_t sm = sizeof(T) == 8 ? zl_smem<double>(m_, tpc) : zl_smem<float>(m_, tpc);
+            if (sm > 227 * 1024) continue;
+            const void* f = nullptr;
+            LB_SWITCH_M(m_, {
+                if (tpc == 1) f = zl_kernel<T, M, 1>();
+                else if (tpc == 2) f = zl_kernel<T, M, 2>();
+                else f = zl_kernel<T, M, 4>();
+            });
+            if (!f) continue;
+            cudaFuncAttributes fa;
+            LB_CK(cudaFuncGetAttributes(&fa, f));
+            if (fa.localSizeBytes > 64) continue;     // a variant that spills more than a few registers is not taken
+            LB_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            int per = 0;
+            LB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, zl_nt(m_, tpc), sm));
+            const int grid = (zf_ntiles_ + tpc - 1) / tpc;
+            if (per >= 1 && grid <= per * nsm) {
+                zf_lines_ = true; zf_tpc_ = tpc; zf_grid_ = grid; zf_smem_ = sm;
+                break;
+            }
+        }
+        for (int tpc = 1; tpc <= 4 && m_ >= 16 && !zf_lines_; tpc *= 2) {
             const size_t sm = sizeof(T) == 8 ? zf_smem<double>(m_, tpc) : zf_smem<float>(m_, tpc);
             if (sm > 227 * 1024) break;
             const void* f = nullptr;
@@ -559,12 +589,19 @@ template <typename T> void Plan<T>::zfused(const C* bold, C* bnew, int check, cu
     void* args[] = {&a};
     const void* f = nullptr;
     LB_SWITCH_M(m_, {
-        if (zf_tpc_ == 1) f = zf_kernel<T, M, 1>();
-        else if (zf_tpc_ == 2) f = zf_kernel<T, M, 2>();
-        else f = zf_kernel<T, M, 4>();
+        if (zf_lines_) {
+            if (zf_tpc_ == 1) f = zl_kernel<T, M, 1>();
+            else if (zf_tpc_ == 2) f = zl_kernel<T, M, 2>();
+            else f = zl_kernel<T, M, 4>();
+        } else {
+            if (zf_tpc_ == 1) f = zf_kernel<T, M, 1>();
+            else if (zf_tpc_ == 2) f = zf_kernel<T, M, 2>();
+            else f = zf_kernel<T, M, 4>();
+        }
     });
+    const int nt = zf_lines_ ? zl_nt(m_, zf_tpc_) : zf_nt(m_, zf_tpc_);
     cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
-    cudaError_t e = cudaLaunchCooperativeKernel(f, dim3(zf_grid_), dim3(zf_nt(m_, zf_tpc_)), args, zf_smem_, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(f, dim3(zf_grid_), dim3(nt), args, zf_smem_, s);
     if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
     if (prof_) prof_->end(K_COLI, e0, s, 4 * sb());
 }

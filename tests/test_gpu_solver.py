@@ -89,8 +89,10 @@ def test_lambda_min_mixed_precision(lbtr):
 
 def test_barrier_timeout_returns_status_without_hang(lbtr):
     # A grid-barrier budget of one cycle makes every waiting block give up at once; the
-    # call must return LB_ERR_TIMEOUT and the context must stay usable afterwards.
-    w = inputs.random_problem((16, 16), 3, sigma=0.3)
+    # call must return LB_ERR_TIMEOUT and the context must stay usable afterwards.  The
+    # grid is 16^3 so that the fused iteration spans several CTAs (a one-CTA grid never
+    # waits at its barriers).
+    w = inputs.random_problem((16, 16, 16), 3, sigma=0.3)
     p = olb.Problem.from_workload(w)
     ctx = _ctx(lbtr, w, lbtr.LB_FP64)
     phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
