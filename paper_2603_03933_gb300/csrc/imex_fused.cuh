@@ -38,6 +38,10 @@ template <typename T> struct ZfArgs {
     double r, rtol, steptol, eps_abs, eps_rel_abs;
     int check, max_iter;
     long long spec_half;      // rows * H: offset of nyq within a spectrum
+    // the tests of each step in the working precision (k_imex_lines)
+    T t_thr_abs2, t_thr_rel2; // (eps_abs eta)^2, (eps_rel_abs eta)^2: residual^2 eta^2 below either = converged
+    T t_r2, t_rtol_r2;        // r^2 and rtol r^2 of the multiplier rule
+    T t_inv_n2;
 };
 
 __host__ __device__ constexpr int zf_nt(int m, int tpc) { return 2 * m * tpc > 1024 ? 1024 : 2 * m * tpc; }
@@ -290,23 +294,29 @@ __device__ __forceinline__ bool newton_update(NewtonState& ns, double phi, doubl
     return !small;
 }
 
-// sum the NQ per-CTA partials of barrier step `stepi` (warp 0) into sh[0..NQ); the loads
-// go to L2 (written by other CTAs before the barrier) and are independent, so they overlap
-template <int NQ>
-__device__ __forceinline__ void zl_gather(const double* P, int stepi, double* sh) {
+// sum the NQ per-CTA partials of barrier step `stepi` (warp 0) into sh[0..NQ), in the
+// partials' own form; the loads go to L2 (written by other CTAs before the barrier) and are
+// independent, so they overlap
+template <typename T, int NQ>
+__device__ __forceinline__ void zl_gather(const Part<T>* P, int stepi, Part<T>* sh) {
     const int G = gridDim.x;
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            double x = 0.0;
+            Part<T> x;
+            part_zero(x);
 #pragma unroll 4
-            for (int b = threadIdx.x; b < G; b += 32) x += __ldcg(&P[(stepi & 1) * 5 * G + k * G + b]);
+            for (int b = threadIdx.x; b < G; b += 32) x = part_add(x, part_ldcg(&P[(stepi & 1) * 5 * G + k * G + b]));
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+            for (int off = 16; off > 0; off >>= 1) x = part_add(x, part_shfl_down(x, off));
             if (threadIdx.x == 0) sh[k] = x;
         }
     }
 }
+
+// correctly rounded reciprocal in the working precision
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 
 template <typename T, int M, int TPC>
 __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(ZfArgs<T> a) {
@@ -323,12 +333,15 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     C* TA = reinterpret_cast<C*>(smem_raw) + (size_t)q * 2 * NL * TS;
     C* TB = TA + NL * TS;
     double* red = reinterpret_cast<double*>(reinterpret_cast<C*>(smem_raw) + (size_t)TPC * 2 * NL * TS);
-    __shared__ double s_sum[2];
-    __shared__ double s_lam;
-    __shared__ T s_el;
+    __shared__ double s_lam, s_lamp;
+    __shared__ T s_el, s_elp;
     __shared__ int s_act;
-    __shared__ double sh[5];
+    __shared__ Part<T> sh[5];
     __shared__ NewtonState ns;
+    if (threadIdx.x == 0) {            // lambda_j and eta lambda_j, read after the first barrier
+        s_lamp = st->lam;
+        s_elp = (T)(a.eta * s_lamp);
+    }
     const int l = lt % NL, i = lt / NL;
     const C zero = mk<T>((T)0, (T)0);
     const T* __restrict__ qt = a.qtab;
@@ -384,13 +397,13 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     const T wgt = (s.kx_const < 0 && kx > 0) ? (T)2 : (T)1;
     const bool k0line = (s.kx_const < 0) && kx == 0 && zo;
     const T* qe = qt + (a.dim == 3 ? 2 * M : M);
-    const T eta = a.eta, n2 = (T)a.inv_n2;
-    const double lam_prev = st->lam;
+    const T eta = a.eta;
     const int j = st->it + 1;
-    const T elp = (T)(a.eta * lam_prev);
+    const T elp = s_elp;
     T aa[L1];
-    const T cw = wgt * n2;
-    Acc<T> acc[5];
+    const T cw = wgt * a.t_inv_n2;
+    // per-thread sums in two interleaved halves (pairwise), then float-float over the grid
+    T sm0[2][5] = {};
 #pragma unroll
     for (int m = 0; m < L1; ++m) {
         const int e = fo(m);
@@ -399,70 +412,86 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         v[m] = x;
         const T tt = (T)1 - (byz + qe[e]);
         const T ai = (T)1 + eta * a.xi2 * tt * tt;
-        const T ci = cw * (x.x * x.x + x.y * x.y);
+        const T x2 = x.x * x.x + x.y * x.y;
+        const T ci = cw * x2;
         aa[m] = ai;
         if (ok) {
             const T dx = old[m].x - x.x, dy = old[m].y - x.y;
-            acc[0].add(wgt * (dx * dx + dy * dy));
-            acc[1].add(wgt * (x.x * x.x + x.y * x.y));
-            const T den = ai + elp;
-            const T qv = ci / (den * den);
-            acc[2].add(ci / (ai * ai));
-            acc[3].add(qv);
-            acc[4].add((T)-2 * eta * qv / den);
+            const T rd = rcp_t(ai + elp), ra = rcp_t(ai);
+            const T qv = ci * rd * rd;
+            sm0[m & 1][0] += wgt * (dx * dx + dy * dy);
+            sm0[m & 1][1] += wgt * x2;
+            sm0[m & 1][2] += ci * ra * ra;
+            sm0[m & 1][3] += qv;
+            sm0[m & 1][4] += (T)-2 * eta * qv * rd;
             a.bnew[base + (long long)e * es] = x;
         }
     }
-    double* P = a.partials;
+    Part<T>* P = reinterpret_cast<Part<T>*>(a.partials);
     const int G = gridDim.x;
     int stepi = 0;
     {
-        double tot[5];
-        block_sum<T, 5>(acc, red, tot);
+        Acc<T> acc[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) { acc[k].add(sm0[0][k]); acc[k].add(sm0[1][k]); }
+        Part<T> tot[5];
+        block_part<T, 5>(acc, red, tot);
         if (threadIdx.x == 0)
             for (int k = 0; k < 5; ++k) P[k * G + blockIdx.x] = tot[k];
     }
     if (!grid_sync(a.bar)) return;
-    zl_gather<5>(P, stepi, sh);
+    zl_gather<T, 5>(P, stepi, sh);
     ++stepi;
     if (threadIdx.x == 0) {
-        double sums[5];
-        for (int k = 0; k < 5; ++k) sums[k] = sh[k] * (k < 2 ? a.inv_n2 : 1.0);
+        // the tests of every iteration in the working precision; double only for Newton steps
+        const T res2 = part_to_T(sh[0], T()) * a.t_inv_n2;        // (eta * residual)^2
+        const T bn2 = part_to_T(sh[1], T()) * a.t_inv_n2;
         int act = ACT_SOLVE;
         // convergence of d_j (not on the initial call, which only sets up lambda_1)
         if (a.check) {
-            const double res = sqrt(fmax(sums[0], 0.0)) / a.eta;
-            const bool bad = !isfinite(res) || !isfinite(sums[1]);
-            const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+            const bool bad = !isfinite(res2) || !isfinite(bn2);
+            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2;
             if (bad || conv || j >= a.max_iter) {
                 if (blockIdx.x == 0) {
-                    st->residual = res;
-                    st->bnorm2 = sums[1];
-                    st->final_lam = lam_prev;
+                    st->residual = (double)(sqrt(res2 > (T)0 ? res2 : (T)0) / eta);
+                    st->bnorm2 = (double)bn2;
+                    st->final_lam = s_lamp;
                     st->final_src = (j - 1) & 1;
                     st->it = j;
                     st->done = bad ? 3 : (conv ? 1 : 2);
                 }
                 act = ACT_RETURN;
             }
-            s_sum[0] = res;
-            s_sum[1] = sums[1];
         }
         if (act != ACT_RETURN) {
-            // the multiplier rule: 0 if phi(0) <= r^2, else Newton from the previous multiplier
-            ns.r = a.r;
-            ns.r2 = a.r * a.r;
-            ns.rtol = a.rtol;
-            ns.steptol = a.steptol;
+            // the multiplier rule: 0 if phi(0) <= r^2, else the root of phi = r^2 by Newton
+            // from the previous multiplier (no step when that one already meets the tolerance)
             ns.newton = 0;
             ns.steps = 0;
-            ns.lam = 0.0;
-            if (!(sums[2] <= ns.r2)) {
-                ns.lam = lam_prev;
-                if (newton_update(ns, lam_prev == 0.0 ? sums[2] : sums[3], sums[4])) act = ACT_EVAL;
+            s_el = elp;
+            s_lam = s_lamp;
+            if (part_to_T(sh[2], T()) <= a.t_r2) {
+                s_lam = 0.0;
+                s_el = (T)0;
+            } else {
+                const Part<T> phip = elp == (T)0 ? sh[2] : sh[3];
+                const T dev = part_to_T(phip, T()) - a.t_r2;
+                if (!(fabs(dev) <= a.t_rtol_r2)) {
+                    ns.r = a.r;
+                    ns.r2 = a.r * a.r;
+                    ns.rtol = a.rtol;
+                    ns.steptol = a.steptol;
+                    ns.lam = s_lamp;
+                    if (newton_update(ns, part_to_double(phip), part_to_double(sh[4]))) act = ACT_EVAL;
+                    s_lam = ns.lam;
+                    s_el = (T)(a.eta * ns.lam);
+                }
             }
-            s_lam = ns.lam;
-            s_el = (T)(a.eta * ns.lam);
+            if (a.check && blockIdx.x == 0) {
+                st->it = j;
+                st->residual = (double)(sqrt(res2 > (T)0 ? res2 : (T)0) / eta);
+                st->bnorm2 = (double)bn2;
+            }
         }
         s_act = act;
     }
@@ -470,25 +499,28 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     if (s_act == ACT_RETURN) return;
     while (s_act == ACT_EVAL) {
         const T el = s_el;
-        Acc<T> ac2[2];
+        T sm1[2][2] = {};
 #pragma unroll
         for (int m = 0; m < L1; ++m) {
-            const T den = aa[m] + el;
-            const T qv = cw * (v[m].x * v[m].x + v[m].y * v[m].y) / (den * den);
-            ac2[0].add(qv);
-            ac2[1].add((T)-2 * eta * qv / den);
+            const T rd = rcp_t(aa[m] + el);
+            const T qv = cw * (v[m].x * v[m].x + v[m].y * v[m].y) * rd * rd;
+            sm1[m & 1][0] += qv;
+            sm1[m & 1][1] += (T)-2 * eta * qv * rd;
         }
-        double t2[2];
-        block_sum<T, 2>(ac2, red, t2);
+        Acc<T> ac2[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) { ac2[k].add(sm1[0][k]); ac2[k].add(sm1[1][k]); }
+        Part<T> t2[2];
+        block_part<T, 2>(ac2, red, t2);
         if (threadIdx.x == 0) {
             P[(stepi & 1) * 5 * G + 0 * G + blockIdx.x] = t2[0];
             P[(stepi & 1) * 5 * G + 1 * G + blockIdx.x] = t2[1];
         }
         if (!grid_sync(a.bar)) return;
-        zl_gather<2>(P, stepi, sh);
+        zl_gather<T, 2>(P, stepi, sh);
         ++stepi;
         if (threadIdx.x == 0) {
-            const bool more = newton_update(ns, sh[0], sh[1]);
+            const bool more = newton_update(ns, part_to_double(sh[0]), part_to_double(sh[1]));
             s_lam = ns.lam;
             s_el = (T)(a.eta * ns.lam);
             s_act = more ? ACT_EVAL : ACT_SOLVE;
@@ -498,11 +530,6 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->lam = s_lam;
         st->newton += ns.newton;
-        if (a.check) {
-            st->it = j;
-            st->residual = s_sum[0];
-            st->bnorm2 = s_sum[1];
-        }
     }
 
     // 4. the implicit diagonal solve and the inverse transform of the columns
@@ -510,7 +537,7 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     const T ks = (T)a.inv_n;
 #pragma unroll
     for (int m = 0; m < L1; ++m) {
-        const T f = ks / (aa[m] + el);
+        const T f = ks * rcp_t(aa[m] + el);
         v[m] = mk<T>(v[m].x * f, v[m].y * f);
     }
 #pragma unroll

@@ -586,6 +586,11 @@ template <typename T> void Plan<T>::zfused(const C* bold, C* bnew, int check, cu
     a.r = r_; a.rtol = rtol_; a.steptol = steptol_; a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_;
     a.check = check; a.max_iter = max_iter_;
     a.spec_half = (long long)rows_ * h_;
+    a.t_thr_abs2 = (T)(eps_abs_ * eta * eps_abs_ * eta);
+    a.t_thr_rel2 = (T)(eps_rel_abs_ * eta * eps_rel_abs_ * eta);
+    a.t_r2 = (T)(r_ * r_);
+    a.t_rtol_r2 = (T)(rtol_ * r_ * r_);
+    a.t_inv_n2 = (T)a.inv_n2;
     void* args[] = {&a};
     const void* f = nullptr;
     LB_SWITCH_M(m_, {

@@ -56,29 +56,74 @@ template <> struct Acc<float> {
     __device__ __forceinline__ void merge(const Acc& o) { v = ff_add(v, o.v); }
 };
 
-// Reduce NQ accumulators over the block; thread 0 receives the totals in out[].
-// scratch: at least 32 * NQ doubles of shared memory.
+// Block and grid partial sums in the accumulator's own form: a float-float pair for the
+// float path (all arithmetic on the FP32 pipe), a double for the double path.
+template <typename T> struct PartOf;
+template <> struct PartOf<float> { using type = ff; };
+template <> struct PartOf<double> { using type = double; };
+template <typename T> using Part = typename PartOf<T>::type;
+
+__device__ __forceinline__ ff part_of(const Acc<float>& a) { return a.v; }
+__device__ __forceinline__ double part_of(const Acc<double>& a) { return a.v; }
+__device__ __forceinline__ void part_zero(ff& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void part_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ ff part_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double part_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff part_shfl_down(ff a, int off) {
+    ff o;
+    o.hi = __shfl_down_sync(0xffffffffu, a.hi, off);
+    o.lo = __shfl_down_sync(0xffffffffu, a.lo, off);
+    return o;
+}
+__device__ __forceinline__ double part_shfl_down(double a, int off) { return __shfl_down_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ double part_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double part_to_double(double a) { return a; }
+__device__ __forceinline__ float part_to_T(ff a, float) { return a.hi + a.lo; }
+__device__ __forceinline__ double part_to_T(double a, double) { return a; }
+// L2 load of a partial written by another block before a grid barrier
+__device__ __forceinline__ ff part_ldcg(const ff* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    ff r;
+    r.hi = v.x;
+    r.lo = v.y;
+    return r;
+}
+__device__ __forceinline__ double part_ldcg(const double* p) { return __ldcg(p); }
+
+// Reduce NQ accumulators over the block; thread 0 receives the totals in out[] in the
+// accumulator's form.  scratch: at least 32 * NQ doubles of shared memory.
 template <typename T, int NQ>
-__device__ __forceinline__ void block_sum(Acc<T> (&a)[NQ], double* scratch, double* out) {
+__device__ __forceinline__ void block_part(Acc<T> (&a)[NQ], double* scratch, Part<T>* out) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a[q].add_shfl(off);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = (blockDim.x + 31) >> 5;
+    Part<T>* sp = reinterpret_cast<Part<T>*>(scratch);
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) scratch[q * 32 + warp] = a[q].get();
+        for (int q = 0; q < NQ; ++q) sp[q * 32 + warp] = part_of(a[q]);
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += scratch[q * 32 + w];
-            out[q] = s;
+            Part<T> t = sp[q * 32];
+            for (int w = 1; w < nw; ++w) t = part_add(t, sp[q * 32 + w]);
+            out[q] = t;
         }
     }
     __syncthreads();
+}
+
+// As block_part, with the totals converted to double (one conversion per quantity).
+template <typename T, int NQ>
+__device__ __forceinline__ void block_sum(Acc<T> (&a)[NQ], double* scratch, double* out) {
+    Part<T> t[NQ];
+    block_part<T, NQ>(a, scratch, t);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) out[q] = part_to_double(t[q]);
 }
 
 // Max-reduction of a non-negative value over the block; thread 0 receives it.
