@@ -100,6 +100,25 @@ lb_status lb_energy_grad(lb_ctx *ctx, const void *phi, double *energy, void *gra
                          double *gmax, lb_stream stream);
 
 /*
+ * Energy and its derivatives with respect to the model parameters and the cell, for
+ * parameter fits and cell optimisation (the paper has no such entry point; the energy is
+ * that of §2, eq. interaction_bulk_energy, with Lambda_k = xi^2 (1 - |Bk|^2)^2 and
+ * B = diag(2 pi / L_a)).  The grid values of phi are held fixed, so the field stretches
+ * with the box:
+ *   out[0] = E,
+ *   out[1] = dE/dtau   = <phi^2 / 2>_N,
+ *   out[2] = dE/dgamma = -<phi^3 / 6>_N,
+ *   out[3 + a] = dE/dL_a = sum_k 1/2 |phi_hat_k|^2 4 xi^2 (1 - |Bk|^2) (Bk)_a^2 / L_a,
+ *                a = x, y, z (out[5] = 0 in 2D); the bulk term does not depend on L.
+ *   phi  [in]  device field, zero mean (checked as in lb_energy_grad).
+ *   out  [out] host array of 6 doubles.
+ *   grad [out] device field or NULL: g as in lb_energy_grad; the derivative of E with
+ *              respect to the grid values of phi, restricted to zero-mean fields, is g / N.
+ * Errors: those of lb_energy_grad; LB_ERR_NONFINITE.  Synchronises the stream.
+ */
+lb_status lb_energy_derivs(lb_ctx *ctx, const void *phi, double *out, void *grad, lb_stream stream);
+
+/*
  * Hessian-vector product (paper §2, grad^2 G = Lambda and grad^2 F = F_N Gamma' F_N^{-1};
  * §3.2, H = D + T and the remark on computing T d by FFT):
  *   Hv = P[F^{-1}(Lambda F v) + F''(phi) v],  F''(u) = tau - gamma u + u^2/2.

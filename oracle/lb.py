@@ -114,6 +114,30 @@ def energy(p: Problem, psi: np.ndarray, direct: bool = False) -> float:
     return g + f
 
 
+def energy_derivatives(p: Problem, psi: np.ndarray):
+    """(dE/dtau, dE/dgamma, [dE/dL_a per array axis]) of E = G + F (eq.
+    `interaction_bulk_energy`) with the grid values of psi held fixed.
+
+    F = (1/N) sum_x F(psi) depends on tau and gamma only: dF/dtau = <psi^2/2>_N,
+    dF/dgamma = -<psi^3/6>_N, and not on the box.  G = 1/2 sum_k Lambda_k |psi_hat_k|^2
+    depends on the box through Lambda_k = xi^2 (1 - |Bk|^2)^2 with (Bk)_a = 2 pi k_a / L_a:
+    d|Bk|^2/dL_a = -2 (Bk)_a^2 / L_a, so dLambda_k/dL_a = 4 xi^2 (1 - |Bk|^2) (Bk)_a^2 / L_a.
+    """
+    psi = np.asarray(psi, np.float64)
+    dtau = float(np.mean(psi ** 2 / 2.0))
+    dgamma = float(-np.mean(psi ** 3 / 6.0))
+    c2 = np.abs(fft.forward(psi)) ** 2
+    t = 1.0 - bk_squared(p)
+    dl = []
+    for a, (m, length) in enumerate(zip(p.shape, p.box)):
+        k = fft.wavenumbers(m).astype(np.float64) * (2.0 * np.pi / length)
+        sh = [1] * len(p.shape)
+        sh[a] = m
+        qa = (k * k).reshape(sh)
+        dl.append(float(np.sum(0.5 * c2 * 4.0 * p.xi ** 2 * t * qa) / length))
+    return dtau, dgamma, dl
+
+
 def apply_lam(p: Problem, u: np.ndarray, direct: bool = False) -> np.ndarray:
     """F^{-1} Lambda F u: the reciprocal-space diagonal applied to a physical field."""
     return fft.inverse(lam(p) * fft.forward(u, direct=direct), direct=direct)

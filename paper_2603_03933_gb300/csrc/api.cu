@@ -152,6 +152,15 @@ lb_status lb_energy_grad(lb_ctx* ctx, const void* phi, double* energy, void* gra
     return ctx->energy_grad<float>(*ctx->p32, (const float*)phi, energy, (float*)grad, gmax, s);
 }
 
+lb_status lb_energy_derivs(lb_ctx* ctx, const void* phi, double* out, void* grad, lb_stream stream) {
+    if (!ctx || !phi || !out) return fail(ctx, LB_ERR_INVALID_ARG, "lb_energy_derivs: null argument");
+    if (!aligned16(phi) || (grad && !aligned16(grad)))
+        return fail(ctx, LB_ERR_INVALID_ARG, "lb_energy_derivs: fields must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->prec == LB_FP64) return ctx->energy_derivs<double>(*ctx->p64, (const double*)phi, out, (double*)grad, s);
+    return ctx->energy_derivs<float>(*ctx->p32, (const float*)phi, out, (float*)grad, s);
+}
+
 lb_status lb_hessvec(lb_ctx* ctx, const void* phi, const void* v, void* hv, lb_stream stream) {
     if (!ctx || !phi || !v || !hv) return fail(ctx, LB_ERR_INVALID_ARG, "lb_hessvec: null argument");
     if (!aligned16(phi) || !aligned16(v) || !aligned16(hv))

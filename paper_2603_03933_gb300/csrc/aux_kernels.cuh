@@ -173,7 +173,7 @@ __global__ void k_secular(SecArgs<T> a) {
 }
 
 // ---- physical-space reductions --------------------------------------------------
-enum RedOp { R_DOT = 0, R_SUMSQ_MAX = 1, R_SUM_SUMSQ = 2 };
+enum RedOp { R_DOT = 0, R_SUMSQ_MAX = 1, R_SUM_SUMSQ = 2, R_POW23 = 3 };
 
 template <typename T> struct PhysRedArgs {
     const T* x;
@@ -183,6 +183,7 @@ template <typename T> struct PhysRedArgs {
 };
 
 // R_DOT: [0] sum x y.  R_SUMSQ_MAX: [0] sum x^2, [1] max |x|.  R_SUM_SUMSQ: [0] sum x, [1] sum x^2.
+// R_POW23: [0] sum x^2, [1] sum x^3.
 template <typename T, int OP>
 __global__ void k_physred(PhysRedArgs<T> a) {
     __shared__ double scr[64];
@@ -193,6 +194,7 @@ __global__ void k_physred(PhysRedArgs<T> a) {
         T x = a.x[i];
         if (OP == R_DOT) acc[0].add(x * a.y[i]);
         else if (OP == R_SUMSQ_MAX) { acc[0].add(x * x); mx = fmax(mx, fabs((double)x)); }
+        else if (OP == R_POW23) { acc[0].add(x * x); acc[1].add(x * x * x); }
         else { acc[0].add(x); acc[1].add(x * x); }
     }
     double tot[2];

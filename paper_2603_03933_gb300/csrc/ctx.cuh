@@ -107,6 +107,29 @@ struct lb_ctx {
         return LB_OK;
     }
 
+    // E and its derivatives with respect to tau, gamma and the box lengths (grid values of phi
+    // held fixed); the gradient into grad when non-null.
+    template <typename T>
+    lb_status energy_derivs(lbtr::Plan<T>& p, const T* phi, double* out, T* grad, cudaStream_t s) {
+        double e = 0.0;
+        lb_status st = energy_grad(p, phi, &e, grad, nullptr, s);
+        if (st) return st;
+        p.phys_reduce(lbtr::R_POW23, phi, nullptr, lbtr::S_RED1, s);
+        double pw[2], bx[3];
+        if ((st = sync_read(pw, p.slot(lbtr::S_RED1), 2, s, "lb_energy_derivs"))) return st;
+        p.box_derivs(phi, s);
+        if ((st = launch_status("lb_energy_derivs"))) return st;
+        if ((st = sync_read(bx, p.slot(lbtr::S_DBOX), 3, s, "lb_energy_derivs"))) return st;
+        const double nn = (double)p.n();
+        out[0] = e;
+        out[1] = 0.5 * pw[0] / nn;            // dE/dtau = <phi^2 / 2>_N
+        out[2] = -pw[1] / (6.0 * nn);         // dE/dgamma = -<phi^3 / 6>_N
+        for (int a = 0; a < 3; ++a) out[3 + a] = a < prob.dim ? bx[a] / prob.box[a] : 0.0;
+        for (int a = 0; a < 6; ++a)
+            if (!std::isfinite(out[a])) { err = "lb_energy_derivs: non-finite result"; return LB_ERR_NONFINITE; }
+        return LB_OK;
+    }
+
     // Algorithm 3 driver.
     template <typename T>
     lb_status subproblem(lbtr::Plan<T>& p, const T* phi, const T* g, double r, const T* d0, const lb_sub_opts& o,

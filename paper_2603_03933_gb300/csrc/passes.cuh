@@ -347,6 +347,7 @@ enum ColMode {
     C_TOP_OUT = 7,   // fwd of T-part, combine out = msc * (Lambda * msc * q + X * kscale), zero k0
     C_MSCALE_IN = 8, // load q, * msc * kscale, zero k0, inv, store dst
     C_SOLVE = 9,     // fwd, * kscale / (Lambda + sigma), zero k0, inv   (PCG preconditioner)
+    C_DBOX = 10,     // fwd only, reduce sum_k w/2 |X|^2 4 xi^2 (1 - |Bk|^2) (Bk)_a^2 * escale, a = x, y, z
 };
 
 struct ColSeg {
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
     using C = cplx<T>;
     constexpr bool PRE = (MODE == C_IMEX_IN || MODE == C_MSCALE_IN);
     constexpr bool POST = (MODE == C_LAM || MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT ||
-                           MODE == C_TOP_OUT || MODE == C_SOLVE);
+                           MODE == C_TOP_OUT || MODE == C_SOLVE || MODE == C_DBOX);
     constexpr bool AUX = (MODE == C_IMEX_OUT || MODE == C_TOP_OUT);
     constexpr bool NEED_Q = PRE || (POST && MODE != C_IMEX_OUT);
     if (a.done && *(volatile const int*)a.done) return;
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
     }
     __syncthreads();
 
-    constexpr int NQ = (MODE == C_IMEX_OUT) ? 2 : 1;
+    constexpr int NQ = (MODE == C_IMEX_OUT) ? 2 : (MODE == C_DBOX) ? 3 : 1;
     Acc<T> acc[NQ];
     // 3. transform, with the reciprocal-space operation of the innermost axis
     if (PRE || MODE == C_INV) {
@@ -525,6 +526,24 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
                 }
                 const T tt = (T)1 - bk2;
                 const T lamk = a.xi2 * tt * tt;
+                if (MODE == C_DBOX) {
+                    // dLambda/dL_a = 4 xi^2 (1 - |Bk|^2) (Bk)_a^2 / L_a; the 1/L_a is applied by the host
+                    const int L = l0 + lm_l;
+                    const int kx = s.kx_const >= 0 ? s.kx_const : (L & (H - 1));
+                    T qy, qz;
+                    if (a.dim == 3) {
+                        qy = qt[M + (s.kx_const >= 0 ? L : (L >> HSH))];
+                        qz = qt[2 * M + e];
+                    } else {
+                        qy = qt[M + e];
+                        qz = (T)0;
+                    }
+                    const T c = (T)2 * wgt * a.xi2 * tt * (val.x * val.x + val.y * val.y);
+                    acc[0].add(c * qt[kx]);
+                    acc[NQ > 1 ? 1 : 0].add(c * qy);
+                    acc[NQ > 2 ? 2 : 0].add(c * qz);
+                    continue;
+                }
                 if (MODE == C_LAM_E || MODE == C_QUAD_E) acc[0].add((T)0.5 * wgt * lamk * (val.x * val.x + val.y * val.y));
                 if (MODE == C_TOP_OUT) {
                     const C q = x[AUX ? t : 0];
@@ -546,7 +565,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
     }
 
     // 4. store
-    if (MODE != C_QUAD_E) {
+    if (MODE != C_QUAD_E && MODE != C_DBOX) {
         if (s.elem_contig) {
 #pragma unroll
             for (int t = 0; t < IT; ++t) {
@@ -562,7 +581,7 @@ __global__ void __launch_bounds__(col_nt(M)) k_cols(ColArgs<T> a) {
             }
         }
     }
-    if (MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT) {
+    if (MODE == C_LAM_E || MODE == C_QUAD_E || MODE == C_IMEX_OUT || MODE == C_DBOX) {
         double tot[NQ];
         block_sum<T, NQ>(acc, red, tot);
         if (threadIdx.x == 0)

@@ -21,7 +21,8 @@ enum Slot {
     S_RED0 = 5,    // generic physical reductions
     S_RED1 = 6,
     S_QUAD = 7,    // G(s) of the ratio test
-    S_COUNT = 8
+    S_DBOX = 8,    // sum_k 1/2 |phi_hat|^2 dLambda/dL_a * L_a, a = x, y, z
+    S_COUNT = 9
 };
 constexpr int SLOT_Q = 4;           // quantities per slot
 
@@ -45,6 +46,8 @@ public:
     // energy pieces into slots S_EF (sum F, sum F', sum phi, sum phi^2) and S_EG (G);
     // gradient into grad (if non-null) and max |g| into S_GMAX
     void energy_grad(const T* phi, T* grad, cudaStream_t s);
+    // sum_k 1/2 |x_hat_k|^2 4 xi^2 (1 - |Bk|^2) (Bk)_a^2 (a = x, y, z) into S_DBOX
+    void box_derivs(const T* x, cudaStream_t s);
     // G(s) = 1/2 sum_k Lambda_k |s_hat_k|^2 into S_QUAD
     void quad_energy(const T* x, cudaStream_t s);
     // physical reductions into slot (R_DOT: sum x y; R_SUMSQ_MAX; R_SUM_SUMSQ)

@@ -135,6 +135,7 @@ template <typename T, int M> cudaError_t set_smem_attrs() {
     setc((const void*)k_cols<T, M, C_TOP_OUT>);
     setc((const void*)k_cols<T, M, C_MSCALE_IN>);
     setc((const void*)k_cols<T, M, C_SOLVE>);
+    setc((const void*)k_cols<T, M, C_DBOX>);
     return e;
 }
 
@@ -386,7 +387,7 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     int grid = a.nb_main + (s1.nlines + COL_NL - 1) / COL_NL;
     a.dim = dim_; a.xi2 = (T)xi2_; a.kscale = kscale; a.escale = escale; a.eta = (T)eta;
     a.sigma = (T)sigma; a.lam = lam;
-    a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : 1, 0u);
+    a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : mode == C_DBOX ? 3 : 1, 0u);
     a.done = done;
     cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     const bool lines = ln_grid_cap_ > 0 && ln_mode_ok(mode) && dst == nullptr && src == nullptr;
@@ -412,6 +413,7 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
             case C_IMEX_OUT: launch_cols<T, M, C_IMEX_OUT>(a, grid, s); break;
             case C_TOP_OUT: launch_cols<T, M, C_TOP_OUT>(a, grid, s); break;
             case C_SOLVE: launch_cols<T, M, C_SOLVE>(a, grid, s); break;
+            case C_DBOX: launch_cols<T, M, C_DBOX>(a, grid, s); break;
             default: launch_cols<T, M, C_MSCALE_IN>(a, grid, s); break;
         }
     });
@@ -515,6 +517,13 @@ template <typename T> void Plan<T>::energy_grad(const T* phi, T* grad, cudaStrea
     }
 }
 
+template <typename T> void Plan<T>::box_derivs(const T* x, cudaStream_t s) {
+    const int inner = dim_ == 3 ? 2 : 1;
+    const double inv_n = 1.0 / (double)n_;
+    fwd_outer(XF_PLAIN, x, nullptr, nullptr, nullptr, nullptr, d_work_, S_RED0, s);
+    cols(inner, C_DBOX, d_work_, nullptr, nullptr, (T)1, inv_n * inv_n, 0.0, nullptr, S_DBOX, s);
+}
+
 template <typename T> void Plan<T>::quad_energy(const T* x, cudaStream_t s) {
     const int inner = dim_ == 3 ? 2 : 1;
     const double inv_n = 1.0 / (double)n_;
@@ -534,6 +543,9 @@ template <typename T> void Plan<T>::phys_reduce(int op, const T* x, const T* y, 
     } else if (op == R_SUMSQ_MAX) {
         a.red = redslot(slot, 2, 2u);
         k_physred<T, R_SUMSQ_MAX><<<grid, 256, 0, s>>>(a);
+    } else if (op == R_POW23) {
+        a.red = redslot(slot, 2, 0u);
+        k_physred<T, R_POW23><<<grid, 256, 0, s>>>(a);
     } else {
         a.red = redslot(slot, 2, 0u);
         k_physred<T, R_SUM_SUMSQ><<<grid, 256, 0, s>>>(a);

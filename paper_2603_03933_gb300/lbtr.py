@@ -80,6 +80,7 @@ SIGNATURES = [
     ("lb_workspace_bytes", ctypes.c_size_t, [_VP]),
     ("lb_set_params", ctypes.c_int, [_VP, _D, _D, _D]),
     ("lb_energy_grad", ctypes.c_int, [_VP, _VP, _DP, _VP, _DP, _VP]),
+    ("lb_energy_derivs", ctypes.c_int, [_VP, _VP, _DP, _VP, _VP]),
     ("lb_hessvec", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     ("lb_default_sub_opts", None, [ctypes.POINTER(lb_sub_opts)]),
     ("lb_tr_subproblem", ctypes.c_int, [_VP, _VP, _VP, _D, _VP, ctypes.POINTER(lb_sub_opts), _VP,
@@ -224,6 +225,15 @@ def lb_energy_grad(ctx: Context, phi, grad=None, stream=None):
                                ctypes.byref(gm) if grad is not None else None, _stream(stream))
     _check(ctx, st, "lb_energy_grad")
     return e.value, (gm.value if grad is not None else None)
+
+
+def lb_energy_derivs(ctx: Context, phi, grad=None, stream=None) -> dict:
+    """E and dE/dtau, dE/dgamma, dE/dL (x, y, z order) at fixed grid values, g into `grad`
+    when given (C: lb_energy_derivs)."""
+    out = (ctypes.c_double * 6)()
+    st = load().lb_energy_derivs(ctx.handle, _ptr(ctx, phi, "phi"), out, _ptr(ctx, grad, "grad"), _stream(stream))
+    _check(ctx, st, "lb_energy_derivs")
+    return {"energy": out[0], "dtau": out[1], "dgamma": out[2], "dL_xyz": [out[3], out[4], out[5]][:ctx.dim]}
 
 
 def lb_hessvec(ctx: Context, phi, v, hv, stream=None):

@@ -1,0 +1,138 @@
+"""Derivatives of the energy with respect to tau, gamma and the box (differentiation workload).
+
+lb_energy_derivs against the FP64 oracle (energy_derivatives, pinned by central differences
+and closed forms in test_oracle_lb.py), the box derivative against central differences of
+the GPU energy, the torch autograd wrapper against central differences with h = 1e-6, and
+a cell optimisation of the {211} cosine field whose optimum is known in closed form.
+Tolerances: FP64 1e-10 relative; MIXED 1e-5 relative (float FFT, float-float reductions).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lb as olb
+from paper_2603_03933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lbtr():
+    from paper_2603_03933_gb300 import build, lbtr as mod
+    build.build(force=False)
+    mod.load()
+    return mod
+
+
+def _cases():
+    w211 = inputs.config_3d_cubic211(16)
+    return [
+        inputs.random_problem((32, 32), 31, sigma=0.3, box=(9.0, 5.0), tau=-0.2, gamma=0.3),
+        inputs.random_problem((16, 16, 16), 32, sigma=0.3, box=(5.0, 6.0, 7.0), tau=-0.1, gamma=0.25),
+        w211,
+        inputs.config_3d_cubic211(64),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(4))
+def test_energy_derivs_match_oracle(lbtr, prec, case):
+    w = _cases()[case]
+    p = olb.Problem.from_workload(w)
+    fp64 = prec == "fp64"
+    dt = torch.float64 if fp64 else torch.float32
+    phi_np = w.phi0 if fp64 else inputs.remove_mean(w.phi0.astype(np.float32).astype(np.float64))
+    ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
+                                        lbtr.LB_FP64 if fp64 else lbtr.LB_MIXED)
+    phi = torch.tensor(phi_np, dtype=dt, device=DEV)
+    grad = torch.empty_like(phi)
+    d = lbtr.lb_energy_derivs(ctx, phi, grad)
+    dtau, dgamma, dl = olb.energy_derivatives(p, phi.double().cpu().numpy())
+    e = olb.energy(p, phi.double().cpu().numpy())
+    tol = 1e-10 if fp64 else 1e-5
+    x = phi.double().cpu().numpy()
+    assert abs(d["energy"] - e) <= (1e-12 if fp64 else 1e-6) * max(1.0, abs(e))
+    assert abs(d["dtau"] - dtau) <= tol * abs(dtau)
+    # sums with cancellation are compared against the sum of the magnitudes of their terms
+    assert abs(d["dgamma"] - dgamma) <= tol * np.mean(np.abs(x) ** 3) / 6.0
+    c2 = np.abs(np.fft.fftn(x) / x.size) ** 2
+    absl = sum(abs(v) for v in dl) + np.sum(c2 * 2.0 * np.abs(1.0 - olb.bk_squared(p))) * max(
+        (2 * math.pi * (m // 2) / length) ** 2 / length for m, length in zip(p.shape, p.box))
+    for a, v in enumerate(reversed(d["dL_xyz"])):        # array-axis order
+        assert abs(v - dl[a]) <= tol * absl, (a, v, dl[a])
+    g = olb.gradient(p, phi.double().cpu().numpy())
+    assert np.max(np.abs(grad.double().cpu().numpy() - g)) <= (1e-10 if fp64 else 2e-5) * np.max(np.abs(g))
+
+
+def test_box_derivative_matches_central_differences_of_gpu_energy(lbtr):
+    w = inputs.random_problem((16, 16, 16), 33, sigma=0.3, box=(5.0, 6.0, 7.0), tau=-0.1, gamma=0.25)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+
+    def energy(box):
+        c = lbtr.lb_create_from_array_box(w.shape, box, w.xi, w.tau, w.gamma, lbtr.LB_FP64)
+        return lbtr.lb_energy_grad(c, phi)[0]
+
+    c = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, lbtr.LB_FP64)
+    dl = list(reversed(lbtr.lb_energy_derivs(c, phi)["dL_xyz"]))
+    for a in range(3):
+        h = 1e-4 * w.box[a]
+        bp = list(w.box); bp[a] += h
+        bm = list(w.box); bm[a] -= h
+        fd = (energy(bp) - energy(bm)) / (2 * h)
+        assert abs(fd - dl[a]) <= 1e-6 * max(abs(dl[a]), 1e-3), (a, fd, dl[a])
+
+
+def test_autograd_matches_central_differences(lbtr):
+    from paper_2603_03933_gb300.autodiff import lb_energy
+    w = inputs.config_3d_cubic211(16)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV, requires_grad=True)
+    tau = torch.tensor(w.tau, dtype=torch.float64, device=DEV, requires_grad=True)
+    gam = torch.tensor(w.gamma, dtype=torch.float64, device=DEV, requires_grad=True)
+    box = torch.tensor(w.box, dtype=torch.float64, device=DEV, requires_grad=True)
+    e = lb_energy(phi, tau, gam, box)
+    e.backward()
+    h = 1e-6
+
+    def f(ph=phi, t=tau, g=gam, b=box):
+        with torch.no_grad():
+            return float(lb_energy(ph.detach(), t.detach(), g.detach(), b.detach()))
+
+    assert abs((f(t=tau + h) - f(t=tau - h)) / (2 * h) - float(tau.grad)) <= 1e-7 * abs(float(tau.grad))
+    assert abs((f(g=gam + h) - f(g=gam - h)) / (2 * h) - float(gam.grad)) <= 1e-6 * abs(float(gam.grad))
+    for a in range(3):
+        ea = torch.zeros(3, dtype=torch.float64, device=DEV)
+        ea[a] = h * float(box[a])
+        fd = (f(b=box + ea) - f(b=box - ea)) / (2 * h * float(box[a]))
+        assert abs(fd - float(box.grad[a])) <= 1e-5 * abs(float(box.grad[a])), (a, fd, float(box.grad[a]))
+    # a zero-mean direction: the field derivative is g / N restricted to zero mean
+    gen = np.random.default_rng(7)
+    dirn = torch.tensor(inputs.remove_mean(gen.standard_normal(w.shape)), dtype=torch.float64, device=DEV)
+    fd = (f(ph=phi + h * dirn) - f(ph=phi - h * dirn)) / (2 * h)
+    an = float((phi.grad * dirn).sum())
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-8)
+
+
+def test_cell_optimisation_of_211_cosines_reaches_unit_reciprocal_length(lbtr):
+    # At fixed grid values, the pure {211} field (|k|^2 = 6) has its energy minimum over a
+    # cubic cell where every mode sits at |Bk| = 1, i.e. at side 2 pi sqrt(6); starting
+    # from the differentiation workload's side 2 pi sqrt(8), a secant iteration on the
+    # isotropic derivative sum_a dE/dL_a reaches it.
+    m = 16
+    phi = torch.tensor(inputs.remove_mean(inputs.cosine_field((m,) * 3, inputs.CUBIC211_INDEX, 0.1)),
+                       dtype=torch.float64, device=DEV)
+
+    def dsum(side):
+        c = lbtr.lb_create_from_array_box((m,) * 3, (side,) * 3, 1.0, -0.1, 0.2, lbtr.LB_FP64)
+        return sum(lbtr.lb_energy_derivs(c, phi)["dL_xyz"])
+
+    l0, l1 = 2 * math.pi * math.sqrt(8.0), 2 * math.pi * math.sqrt(7.5)
+    f0, f1 = dsum(l0), dsum(l1)
+    for _ in range(30):
+        if abs(f1) < 1e-14 or f1 == f0:
+            break
+        l0, l1, f0 = l1, l1 - f1 * (l1 - l0) / (f1 - f0), f1
+        f1 = dsum(l1)
+    assert abs(l1 - 2 * math.pi * math.sqrt(6.0)) <= 1e-8

@@ -121,3 +121,57 @@ def test_t_and_d_split_sum_to_hessian():
     v = inputs.gaussian_field(w.shape, 1.0, 32)
     h = lb.hessvec(p, w.phi0, v)
     assert np.allclose(lb.apply_D(p, v) + lb.apply_T(p, w.phi0, v), h, atol=1e-12 * np.max(np.abs(h)))
+
+
+# ---- derivatives with respect to tau, gamma and the box (differentiation workload) ----
+
+def _with(p, **kw):
+    d = dict(shape=p.shape, box=p.box, xi=p.xi, tau=p.tau, gamma=p.gamma)
+    d.update(kw)
+    return lb.Problem(**d)
+
+
+@pytest.mark.parametrize("shape,box", [((8, 8, 8), (5.0, 6.0, 7.0)), ((16, 16), (9.0, 6.5))])
+def test_energy_derivatives_match_central_differences(shape, box):
+    # E is linear in tau and gamma, so their central differences are exact up to rounding;
+    # along L_a the central difference has an h^2 error (h = 1e-4 L_a relative, tol 1e-6).
+    w = inputs.random_problem(shape, 21, sigma=0.4, box=box, tau=-0.15, gamma=0.35)
+    p = lb.Problem.from_workload(w)
+    dtau, dgamma, dl = lb.energy_derivatives(p, w.phi0)
+    h = 1e-3
+    fd_tau = (lb.energy(_with(p, tau=p.tau + h), w.phi0) - lb.energy(_with(p, tau=p.tau - h), w.phi0)) / (2 * h)
+    fd_gam = (lb.energy(_with(p, gamma=p.gamma + h), w.phi0) - lb.energy(_with(p, gamma=p.gamma - h), w.phi0)) / (2 * h)
+    assert abs(fd_tau - dtau) <= 1e-10 * max(1.0, abs(dtau))
+    assert abs(fd_gam - dgamma) <= 1e-10 * max(1.0, abs(dgamma))
+    for a in range(len(shape)):
+        hl = 1e-4 * box[a]
+        bp = list(box); bp[a] += hl
+        bm = list(box); bm[a] -= hl
+        fd = (lb.energy(_with(p, box=tuple(bp)), w.phi0) - lb.energy(_with(p, box=tuple(bm)), w.phi0)) / (2 * hl)
+        assert abs(fd - dl[a]) <= 1e-6 * max(abs(dl[a]), 1e-3), (a, fd, dl[a])
+
+
+def test_box_derivative_of_a_single_mode_closed_form():
+    # psi = 2A cos(2 pi k x / L_x): G = Lambda_q A^2 with q = (2 pi k / L_x)^2, so
+    # dE/dL_x = A^2 xi^2 2 (1 - q) 2 q / L_x and dE/dL_y = 0
+    m, k, amp, xi, lx, ly = 16, 3, 0.2, 1.3, 11.0, 7.0
+    x = np.arange(m)
+    psi = np.tile(2 * amp * np.cos(2 * np.pi * k * x / m), (m, 1))        # [y][x]
+    p = lb.Problem((m, m), (ly, lx), xi, -0.1, 0.2)
+    _, _, dl = lb.energy_derivatives(p, psi)
+    q = (2 * np.pi * k / lx) ** 2
+    assert abs(dl[1] - amp ** 2 * xi ** 2 * 4 * (1 - q) * q / lx) <= 1e-12
+    assert abs(dl[0]) <= 1e-14
+
+
+def test_211_cosines_are_stationary_in_the_box_at_unit_reciprocal_length():
+    # the 24 {211} vectors have |k|^2 = 6, so on the cubic box of side 2 pi sqrt(6) every
+    # mode sits at |Bk| = 1, where Lambda and dLambda/dL vanish: dE/dL = 0 on every axis,
+    # while the differentiation workload's side 2 pi sqrt(8) is not stationary
+    m = 8
+    psi = inputs.remove_mean(inputs.cosine_field((m, m, m), inputs.CUBIC211_INDEX, 0.1))
+    side6, side8 = 2 * math.pi * math.sqrt(6.0), 2 * math.pi * math.sqrt(8.0)
+    _, _, dl6 = lb.energy_derivatives(lb.Problem((m,) * 3, (side6,) * 3, 1.0, -0.1, 0.2), psi)
+    _, _, dl8 = lb.energy_derivatives(lb.Problem((m,) * 3, (side8,) * 3, 1.0, -0.1, 0.2), psi)
+    assert max(abs(v) for v in dl6) <= 1e-14
+    assert min(abs(v) for v in dl8) > 1e-4
