@@ -36,10 +36,10 @@ L2_BYTES = 129 * 1024 * 1024
 # ncu DRAM traffic per launch of a kernel class, with the hash of the CUDA sources it
 # was captured from (a traffic figure is reported only while the sources match).
 TRAFFIC = {
-    # k_plane_fwd<float,128,XF_HVPMEAN>, k_cols<float,128,C_LAM>, k_plane_inv<float,128,XI_HVP>
-    "xfwd": (16817920, "6bf0cb0e8b6ae985"),
-    "col_inner": (8546304, "6bf0cb0e8b6ae985"),
-    "xinv": (25317888, "6bf0cb0e8b6ae985"),
+    # k_plane_fwd<float,128,XF_HVPMEAN>, k_lines<float,128,C_LAM>, k_plane_inv<float,128,XI_HVP>
+    "xfwd": (16826112, "052906cd0abad65b"),
+    "col_inner": (8550400, "052906cd0abad65b"),
+    "xinv": (25326080, "052906cd0abad65b"),
 }
 
 
