@@ -30,6 +30,7 @@ template <typename T> struct SecArgs {
     double inv_n2;            // 1/N^2
     double eta, r, rtol, steptol;
     double eps_abs, eps_rel_abs;  // stop when residual < max(eps_abs, eps_rel_abs)
+    double floor2;            // or when ||b_{j-1} - b_j||^2 <= floor2 ||b_j||^2 (working-precision floor)
     int check;                // 0 on the initial call (no iterate to check)
     int max_iter;
     T xi2;
@@ -118,7 +119,7 @@ __global__ void k_secular(SecArgs<T> a) {
     if (a.check) {
         double res = sqrt(fmax(a.res[0], 0.0)) / a.eta;
         bool bad = !isfinite(res) || !isfinite(a.res[1]);
-        bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+        bool conv = res < a.eps_abs || res < a.eps_rel_abs || a.res[0] <= a.floor2 * a.res[1];
         if (bad || conv || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;

@@ -36,12 +36,14 @@ template <typename T> struct ZfArgs {
     T xi2, eta;
     double inv_n, inv_n2;
     double r, rtol, steptol, eps_abs, eps_rel_abs;
+    double floor2;            // also converged when ||b_{j-1} - b_j||^2 <= floor2 ||b_j||^2
     int check, max_iter;
     long long spec_half;      // rows * H: offset of nyq within a spectrum
     // the tests of each step in the working precision (k_imex_lines)
     T t_thr_abs2, t_thr_rel2; // (eps_abs eta)^2, (eps_rel_abs eta)^2: residual^2 eta^2 below either = converged
     T t_r2, t_rtol_r2;        // r^2 and rtol r^2 of the multiplier rule
     T t_inv_n2;
+    T t_floor2;
 };
 
 __host__ __device__ constexpr int zf_nt(int m, int tpc) { return 2 * m * tpc > 1024 ? 1024 : 2 * m * tpc; }
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
     if (a.check) {
         const double res = sqrt(fmax(sums[0], 0.0)) / a.eta;
         const bool bad = !isfinite(res) || !isfinite(sums[1]);
-        const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+        const bool conv = res < a.eps_abs || res < a.eps_rel_abs || sums[0] <= a.floor2 * sums[1];
         if (bad || conv || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         // convergence of d_j (not on the initial call, which only sets up lambda_1)
         if (a.check) {
             const bool bad = !isfinite(res2) || !isfinite(bn2);
-            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2;
+            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2 || res2 <= a.t_floor2 * bn2;
             if (bad || conv || j >= a.max_iter) {
                 if (blockIdx.x == 0) {
                     st->residual = (double)(sqrt(res2 > (T)0 ? res2 : (T)0) / eta);
