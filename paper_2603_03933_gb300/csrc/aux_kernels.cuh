@@ -16,7 +16,20 @@ struct ImexState {
     int done;            // 0 running, 1 converged, 2 iteration cap, 3 non-finite
     int final_src;       // which B buffer holds b_{j-1} of the returned iterate
     int pad;
+    double best2;        // smallest (eta residual)^2 seen by the stall test, and its iteration
+    int best_it;         //   (0: none yet)
+    int pad2;
 };
+
+// Stall test of the float inner iteration: the residual counts as improved when it falls
+// below 0.98 of the best squared value so far; no improvement in `k` checked iterations
+// (k > 0) ends the iteration.  Returns the stall flag and updates (best2, best_it).
+__device__ __forceinline__ bool stall_update(int k, int j, double res2, double& best2, int& best_it) {
+    if (k <= 0) return false;
+    const bool stall = best_it > 0 && j - best_it > k;
+    if (best_it == 0 || res2 < 0.98 * best2) { best2 = res2; best_it = j; }
+    return stall;
+}
 
 template <typename T> struct SecArgs {
     const cplx<T>* bmain;     // b_j (unnormalised DFT), zero k = 0
@@ -30,7 +43,7 @@ template <typename T> struct SecArgs {
     double inv_n2;            // 1/N^2
     double eta, r, rtol, steptol;
     double eps_abs, eps_rel_abs;  // stop when residual < max(eps_abs, eps_rel_abs)
-    double floor2;            // or when ||b_{j-1} - b_j||^2 <= floor2 ||b_j||^2 (working-precision floor)
+    int stall;                // or after this many checked iterations without progress (0: off)
     int check;                // 0 on the initial call (no iterate to check)
     int max_iter;
     T xi2;
@@ -116,10 +129,13 @@ __global__ void k_secular(SecArgs<T> a) {
     if (*(volatile int*)&st->done) return;
     const double lam_prev = st->lam;
     const int j = st->it + 1;          // iteration that produced b_j (device-side count)
+    double best2 = st->best2;
+    int best_it = st->best_it;
     if (a.check) {
         double res = sqrt(fmax(a.res[0], 0.0)) / a.eta;
         bool bad = !isfinite(res) || !isfinite(a.res[1]);
-        bool conv = res < a.eps_abs || res < a.eps_rel_abs || a.res[0] <= a.floor2 * a.res[1];
+        const bool stall = stall_update(a.stall, j, a.res[0], best2, best_it);
+        bool conv = res < a.eps_abs || res < a.eps_rel_abs || stall;
         if (bad || conv || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;
@@ -166,10 +182,10 @@ __global__ void k_secular(SecArgs<T> a) {
             dphi = tot[2];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {       // after the grid barriers: every block has read st
         st->lam = lam;
         st->newton += newton;
-        if (a.check) st->it = j;
+        if (a.check) { st->it = j; st->best2 = best2; st->best_it = best_it; }
     }
 }
 

@@ -36,14 +36,13 @@ template <typename T> struct ZfArgs {
     T xi2, eta;
     double inv_n, inv_n2;
     double r, rtol, steptol, eps_abs, eps_rel_abs;
-    double floor2;            // also converged when ||b_{j-1} - b_j||^2 <= floor2 ||b_j||^2
+    int stall;                // also stop after this many checked iterations without progress (0: off)
     int check, max_iter;
     long long spec_half;      // rows * H: offset of nyq within a spectrum
     // the tests of each step in the working precision (k_imex_lines)
     T t_thr_abs2, t_thr_rel2; // (eps_abs eta)^2, (eps_rel_abs eta)^2: residual^2 eta^2 below either = converged
     T t_r2, t_rtol_r2;        // r^2 and rtol r^2 of the multiplier rule
     T t_inv_n2;
-    T t_floor2;
 };
 
 __host__ __device__ constexpr int zf_nt(int m, int tpc) { return 2 * m * tpc > 1024 ? 1024 : 2 * m * tpc; }
@@ -101,6 +100,8 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
     const T eta = a.eta, n2 = (T)a.inv_n2;
     const double lam_prev = st->lam;
     const int j = st->it + 1;
+    double best2 = st->best2;          // read before the first barrier; block 0 writes after it
+    int best_it = st->best_it;
     T cc[IT], aa[IT];
     Acc<T> acc[5];
     const T elp = (T)(a.eta * lam_prev);
@@ -172,7 +173,9 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
     if (a.check) {
         const double res = sqrt(fmax(sums[0], 0.0)) / a.eta;
         const bool bad = !isfinite(res) || !isfinite(sums[1]);
-        const bool conv = res < a.eps_abs || res < a.eps_rel_abs || sums[0] <= a.floor2 * sums[1];
+        const bool stall = stall_update(a.stall, j, sums[0], best2, best_it);
+        if (blockIdx.x == 0 && threadIdx.x == 0) { st->best2 = best2; st->best_it = best_it; }
+        const bool conv = res < a.eps_abs || res < a.eps_rel_abs || stall;
         if (bad || conv || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;
@@ -340,9 +343,13 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     __shared__ int s_act;
     __shared__ Part<T> sh[5];
     __shared__ NewtonState ns;
-    if (threadIdx.x == 0) {            // lambda_j and eta lambda_j, read after the first barrier
+    __shared__ double s_best2;
+    __shared__ int s_best_it;
+    if (threadIdx.x == 0) {            // state of iteration j, read before block 0 updates it
         s_lamp = st->lam;
         s_elp = (T)(a.eta * s_lamp);
+        s_best2 = st->best2;
+        s_best_it = st->best_it;
     }
     const int l = lt % NL, i = lt / NL;
     const C zero = mk<T>((T)0, (T)0);
@@ -452,7 +459,11 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         // convergence of d_j (not on the initial call, which only sets up lambda_1)
         if (a.check) {
             const bool bad = !isfinite(res2) || !isfinite(bn2);
-            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2 || res2 <= a.t_floor2 * bn2;
+            double best2 = s_best2;
+            int best_it = s_best_it;
+            const bool stall = stall_update(a.stall, j, (double)res2, best2, best_it);
+            if (blockIdx.x == 0) { st->best2 = best2; st->best_it = best_it; }
+            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2 || stall;
             if (bad || conv || j >= a.max_iter) {
                 if (blockIdx.x == 0) {
                     st->residual = (double)(sqrt(res2 > (T)0 ? res2 : (T)0) / eta);

@@ -134,10 +134,11 @@ private:
     long long budget_ = kDefaultBudget;
     // imex parameters of the current solve
     double r_ = 0, eps_abs_ = 0, eps_rel_abs_ = 0, rtol_ = 0, steptol_ = 0;
-    // The IMEX residual is ||b_{j-1} - b_j|| / eta; in float it cannot fall below the
-    // rounding of b (~1e-7 ||b||), so the float path also stops once successive b agree to
-    // 16 float epsilons (squared here).  0 in double: the paper's tests alone.
-    static double floor2() { return sizeof(T) == 4 ? (16.0 * 1.1920929e-7) * (16.0 * 1.1920929e-7) : 0.0; }
+    // The IMEX residual is ||b_{j-1} - b_j|| / eta; in float it stops falling at the rounding
+    // level of b, which can lie above the requested tolerance.  The float path therefore
+    // also ends after 512 checked iterations without progress (stall_update); 0 in double:
+    // the paper's tests alone.
+    static int stall_k() { return sizeof(T) == 4 ? 512 : 0; }
     int max_iter_ = 0;
 
     // device memory

@@ -564,7 +564,7 @@ template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaSt
     a.dim = dim_; a.m = m_; a.rows = rows_;
     a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
     a.eta = eta; a.r = r_; a.rtol = rtol_; a.steptol = steptol_;
-    a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_; a.floor2 = floor2();
+    a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_; a.stall = stall_k();
     a.check = check; a.max_iter = max_iter_;
     a.xi2 = (T)xi2_;
     void* args[] = {&a};
@@ -596,8 +596,7 @@ template <typename T> void Plan<T>::zfused(const C* bold, C* bnew, int check, cu
     a.xi2 = (T)xi2_; a.eta = (T)eta;
     a.inv_n = 1.0 / (double)n_; a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
     a.r = r_; a.rtol = rtol_; a.steptol = steptol_; a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_;
-    a.floor2 = floor2();
-    a.t_floor2 = (T)a.floor2;
+    a.stall = stall_k();
     a.check = check; a.max_iter = max_iter_;
     a.spec_half = (long long)rows_ * h_;
     a.t_thr_abs2 = (T)(eps_abs_ * eta * eps_abs_ * eta);
