@@ -33,20 +33,24 @@ METRIC = "Hessian-vector products/s & TR iters/s at 128³, mixed vs FP64 GPU; HB
 UNIT = "HVP/s"
 L2_BYTES = 129 * 1024 * 1024
 
-# ncu DRAM traffic per launch of a kernel class, with the hash of the CUDA sources it
-# was captured from (a traffic figure is reported only while the sources match).
+# ncu DRAM traffic per launch of a kernel class, with the hash of the kernel sources it
+# was captured from (a traffic figure is reported only while those sources match).
 TRAFFIC = {
     # k_plane_fwd<float,128,XF_HVPMEAN>, k_lines<float,128,C_LAM>, k_plane_inv<float,128,XI_HVP>
-    "xfwd": (16826112, "052906cd0abad65b"),
-    "col_inner": (8550400, "052906cd0abad65b"),
-    "xinv": (25326080, "052906cd0abad65b"),
+    "xfwd": (16826112, "b97ac0836c2f78ef"),
+    "col_inner": (8550400, "b97ac0836c2f78ef"),
+    "xinv": (25326080, "b97ac0836c2f78ef"),
 }
+
+
+# the sources that define the HVP kernels (their DRAM traffic is keyed to these)
+HVP_KERNEL_SOURCES = ("common.cuh", "fft_core.cuh", "reduce.cuh", "passes.cuh", "planes.cuh", "lines.cuh")
 
 
 def csrc_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2603_03933_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in HVP_KERNEL_SOURCES:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
