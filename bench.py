@@ -139,14 +139,27 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_max: float, world: int) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling: every
+    replica processes the same number of units)."""
+    return units_per_rank * world / seconds_max
+
+
+def shard(n_items: int, rank: int, world: int) -> list:
+    """Items of an independent batch (e.g. sweep instances) owned by `rank`: round-robin,
+    disjoint across ranks and covering all items."""
+    return list(range(rank, n_items, world))
 
 
 def oracle_hvp_rate(M: int, seconds: float = 12.0) -> dict:
@@ -324,7 +337,7 @@ def main():
     clk = clocks.stop()
     dt = max_over_ranks(dt, world)
     hvps = args.batch * args.steps * world
-    value = hvps / dt
+    value = whole_job_rate(args.batch * args.steps, dt, world)
 
     if args.profile_sub > 0:
         # per-kernel-class times of a fixed number of IMEX inner iterations (Algorithm 3)
