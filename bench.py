@@ -294,6 +294,46 @@ def time_tr(lbtr, w, prec: str, outer: int) -> dict:
     return out
 
 
+def time_sweep(lbtr, rank: int, world: int, n_instances: int, replays: int = 20) -> dict:
+    """The batched 2D sweep (256 instances, M in {64..512}, mixed): every instance's
+    Hessian-vector product as one CUDA graph (lb_batch_hessvec), timed over `replays`
+    replays with CUDA events after 3 warm-up replays; instances are sharded across ranks."""
+    import torch
+    from paper_2603_03933_gb300 import inputs
+    ws = [inputs.batched_sweep(n_instances)[i] for i in shard(n_instances, rank, world)]
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    t0 = time.perf_counter()
+    batch = lbtr.lb_batch_create(probs, lbtr.LB_MIXED)
+    setup_s = time.perf_counter() - t0
+    phis = [torch.tensor(w.phi0, dtype=torch.float32, device="cuda") for w in ws]
+    vs = [torch.tensor(inputs.gaussian_field(w.shape, 1.0, 5000 + i), dtype=torch.float32, device="cuda")
+          for i, w in enumerate(ws)]
+    hvs = [torch.empty_like(v) for v in vs]
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        lbtr.lb_batch_hessvec(batch, phis, vs, hvs, stream=s)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(replays):
+        lbtr.lb_batch_hessvec(batch, phis, vs, hvs, stream=s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    dt = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world)
+    npts = sum(w.n_points for w in ws)
+    sizes = {}
+    for w in ws:
+        sizes[w.shape[0]] = sizes.get(w.shape[0], 0) + 1
+    return {"workload": f"{n_instances} 2D instances, M in {{64,128,256,512}} (seed 5), mixed; "
+                        "one CUDA graph of all instances' Hessian-vector products per replay",
+            "value": whole_job_rate(len(ws) * replays, dt, world), "unit": "instance-HVP/s",
+            "alg_gbs": whole_job_rate(12.0 * npts * replays, dt, world) / 1e9,
+            "us_per_replay": 1e6 * dt / replays, "instances_per_rank": len(ws), "sizes": sizes,
+            "setup_s": setup_s, "gpu_launches": 3 * len(ws) * replays}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,6 +347,8 @@ def main():
                     help="time only the mixed HVP at --size (small runs for profilers)")
     ap.add_argument("--pool", type=int, default=0, help="override the number of (phi, v, Hv) triples")
     ap.add_argument("--tr-outer", type=int, default=4, help="outer IMEX-TR iterations timed per precision")
+    ap.add_argument("--sweep-instances", type=int, default=256,
+                    help="instances of the batched 2D sweep timed as one CUDA graph (0: skip)")
     ap.add_argument("--profile-sub", type=int, default=0,
                     help="profile this many IMEX inner iterations per precision and exit")
     args = ap.parse_args()
@@ -469,7 +511,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_hvp_rate(M)
 
-    launches_per_hvp = 5
+    # kernels per HVP: x/y plane pass, z line pass, inverse plane pass (3D 32^3-128^3); else
+    # x rows, y lines, z lines (with Lambda), y lines, inverse x rows
+    launches_per_hvp = 3 if 32 <= M <= 128 else 5
+    sweep = time_sweep(lbtr, rank, world, args.sweep_instances) if args.sweep_instances > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
@@ -480,7 +525,7 @@ def main():
                    "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_hvp * args.batch * args.steps,
-        "fp64": fp64, "size_256": big, "tr": tr,
+        "fp64": fp64, "size_256": big, "tr": tr, "sweep": sweep,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

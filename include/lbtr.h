@@ -275,6 +275,35 @@ lb_status lb_profile_enable(lb_ctx *ctx, int enable);
 lb_status lb_profile_read(lb_ctx *ctx, int kclass, double *total_ms, long long *launches,
                           double *alg_bytes);
 
+/*
+ * Batches of independent problems, for parameter sweeps (SURVEY-planned phase-diagram
+ * sweep over (tau, gamma, M); the paper solves one problem at a time and has no batch
+ * interface).  A batch owns one context per problem; the problems may differ in grid
+ * size, dimension, box and parameters, and share the precision.
+ *   probs [in]  `count` problem descriptions (copied).
+ *   out   [out] the batch; destroy with lb_batch_destroy.
+ * Errors: those of lb_create; LB_ERR_INVALID_ARG for count <= 0.
+ */
+typedef struct lb_batch lb_batch;
+lb_status lb_batch_create(const lb_problem *probs, int count, lb_precision prec, lb_batch **out);
+void lb_batch_destroy(lb_batch *batch);
+const char *lb_batch_last_error(const lb_batch *batch);
+int lb_batch_size(const lb_batch *batch);
+
+/*
+ * hv[i] = H_i v[i] for every problem i of the batch (each as lb_hessvec).  phi, v, hv:
+ * host arrays of lb_batch_size() device pointers, fields laid out as in lb_hessvec.
+ * The first call with a given set of pointers records the products of all problems as
+ * one CUDA graph (independent branches on up to 16 internal streams, largest problems
+ * first on the least-loaded stream); later calls with the same pointers replay it, and a
+ * call with other pointers records anew.  The graph is launched on `stream`; the call is
+ * asynchronous.  Calls on the same batch must not overlap on the GPU (the problems'
+ * contexts hold the scratch spectra).
+ * Errors: LB_ERR_INVALID_ARG (null, misaligned or aliased fields), LB_ERR_CUDA.
+ */
+lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *const *v, void *const *hv,
+                           lb_stream stream);
+
 /* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
  * (0 restores the default of about two seconds).  Lets tests exercise the
  * LB_ERR_TIMEOUT path without a hang. */

@@ -94,6 +94,11 @@ SIGNATURES = [
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
     ("lb_hessvec_noalloc", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, _VP, _VP, _VP, _VP]),
+    ("lb_batch_create", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("lb_batch_destroy", None, [_VP]),
+    ("lb_batch_last_error", ctypes.c_char_p, [_VP]),
+    ("lb_batch_size", ctypes.c_int, [_VP]),
+    ("lb_batch_hessvec", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
 ]
 KERNEL_CLASSES = ["xfwd", "xinv", "xmid", "col_y", "col_inner", "secular", "reduce"]
 
@@ -344,3 +349,62 @@ def lb_hessvec_noalloc(dim: int, n: int, box, xi: float, tau: float, gamma: floa
     if st != 0:
         raise LBError(st, "lb_hessvec_noalloc")
     return hv
+
+
+class Batch:
+    """An lb_batch* (independent problems whose products run as one CUDA graph)."""
+
+    def __init__(self, handle, contexts_meta, precision):
+        self.handle = handle
+        self.meta = contexts_meta          # (dim, n) per problem
+        self.precision = precision
+
+    def __len__(self):
+        return len(self.meta)
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.lb_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lb_batch_create(problems, precision: int = LB_FP64) -> Batch:
+    """problems: sequence of (dim, n, box_xyz, xi, tau, gamma) (C: lb_batch_create)."""
+    lib = load()
+    arr = (lb_problem * len(problems))()
+    meta = []
+    for i, (dim, n, box, xi, tau, gamma) in enumerate(problems):
+        box = list(box) + [1.0] * (3 - len(box))
+        arr[i] = lb_problem(dim, n, (ctypes.c_double * 3)(*box[:3]), xi, tau, gamma)
+        meta.append((dim, n))
+    h = ctypes.c_void_p()
+    st = lib.lb_batch_create(arr, len(problems), precision, ctypes.byref(h))
+    if st != 0:
+        raise LBError(st, "lb_batch_create")
+    return Batch(h, meta, precision)
+
+
+def lb_batch_hessvec(batch: Batch, phis, vs, hvs, stream=None):
+    """hvs[i] = H_i vs[i] for every problem, as one CUDA graph (C: lb_batch_hessvec)."""
+    torch = _torch()
+    want = torch.float64 if batch.precision == LB_FP64 else torch.float32
+    n = len(batch)
+    if not (len(phis) == len(vs) == len(hvs) == n):
+        raise ValueError("one phi, v and hv per problem")
+    ptrs = []
+    for group in (phis, vs, hvs):
+        arr = (_VP * n)()
+        for i, t in enumerate(group):
+            dim, m = batch.meta[i]
+            if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != m ** dim:
+                raise ValueError(f"field {i}: need a contiguous {want} CUDA tensor of {m ** dim} values")
+            arr[i] = t.data_ptr()
+        ptrs.append(arr)
+    st = load().lb_batch_hessvec(batch.handle, ptrs[0], ptrs[1], ptrs[2], _stream(stream))
+    if st != 0:
+        msg = load().lb_batch_last_error(batch.handle)
+        raise LBError(st, "lb_batch_hessvec: " + (msg.decode() if msg else ""))
+    return hvs

@@ -1,0 +1,81 @@
+"""Batches of independent problems (the phase-diagram sweep) through lb_batch_hessvec.
+
+Every product of the batch must equal the product of the same problem through its own
+context (lb_hessvec: the same kernels, so the same result up to the rounding tolerance
+of the parity tests), on the recording call, on a replay of the recorded graph, and after
+new field pointers force a new recording; two members are also checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import lb as olb
+from paper_2603_03933_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lbtr():
+    from paper_2603_03933_gb300 import build, lbtr as mod
+    build.build(force=False)
+    mod.load()
+    return mod
+
+
+def _members():
+    ws = inputs.batched_sweep(10, seed=11, sizes=(16, 32, 64, 128, 256))
+    ws.append(inputs.random_problem((32, 32, 32), 12, sigma=0.3, box=(5.0, 6.0, 7.0)))
+    ws.append(inputs.random_problem((64, 64, 64), 13, sigma=0.3))
+    return ws
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_single_problem_products(lbtr, prec):
+    p = lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    ws = _members()
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, p)
+    assert len(batch) == len(ws)
+    phis = [torch.tensor(w.phi0, dtype=dt, device=DEV) for w in ws]
+    vs = [torch.tensor(inputs.gaussian_field(w.shape, 1.0, 900 + i), dtype=dt, device=DEV) for i, w in enumerate(ws)]
+    refs = []
+    for w, phi, v in zip(ws, phis, vs):
+        c = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, p)
+        hv = torch.empty_like(v)
+        lbtr.lb_hessvec(c, phi, v, hv)
+        refs.append(hv)
+    torch.cuda.synchronize()
+    for rnd in range(3):
+        # rounds 0 and 1 share pointers (record, replay); round 2 uses new outputs (record anew)
+        hvs = [torch.full_like(v, float("nan")) for v in vs] if rnd != 1 else hvs
+        if rnd == 1:
+            for h in hvs:
+                h.fill_(float("nan"))
+        lbtr.lb_batch_hessvec(batch, phis, vs, hvs)
+        torch.cuda.synchronize()
+        for i, (h, r) in enumerate(zip(hvs, refs)):
+            assert _rel(h.double().cpu().numpy(), r.double().cpu().numpy()) <= tol, (rnd, i)
+    # two members against the oracle (parity tolerances)
+    for i in (0, len(ws) - 2):
+        w = ws[i]
+        pr = olb.Problem.from_workload(w)
+        ref = olb.hessvec(pr, phis[i].double().cpu().numpy(), vs[i].double().cpu().numpy())
+        assert _rel(hvs[i].double().cpu().numpy(), ref) <= (1e-12 if prec == "fp64" else 2e-5)
+
+
+def test_batch_rejects_bad_fields(lbtr):
+    ws = _members()[:2]
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, lbtr.LB_FP64)
+    f = [torch.zeros(w.shape, dtype=torch.float64, device=DEV) for w in ws]
+    with pytest.raises(lbtr.LBError) as e:
+        lbtr.lb_batch_hessvec(batch, f, f, f)          # outputs alias inputs
+    assert e.value.status == 1
