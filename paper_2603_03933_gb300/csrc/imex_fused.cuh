@@ -299,26 +299,6 @@ __device__ __forceinline__ bool newton_update(NewtonState& ns, double phi, doubl
     return !small;
 }
 
-// sum the NQ per-CTA partials of barrier step `stepi` (warp 0) into sh[0..NQ), in the
-// partials' own form; the loads go to L2 (written by other CTAs before the barrier) and are
-// independent, so they overlap
-template <typename T, int NQ>
-__device__ __forceinline__ void zl_gather(const Part<T>* P, int stepi, Part<T>* sh) {
-    const int G = gridDim.x;
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            Part<T> x;
-            part_zero(x);
-#pragma unroll 4
-            for (int b = threadIdx.x; b < G; b += 32) x = part_add(x, part_ldcg(&P[(stepi & 1) * 5 * G + k * G + b]));
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x = part_add(x, part_shfl_down(x, off));
-            if (threadIdx.x == 0) sh[k] = x;
-        }
-    }
-}
-
 // correctly rounded reciprocal in the working precision
 __device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
@@ -438,19 +418,14 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     }
     Part<T>* P = reinterpret_cast<Part<T>*>(a.partials);
     const int G = gridDim.x;
-    int stepi = 0;
     {
         Acc<T> acc[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) { acc[k].add(sm0[0][k]); acc[k].add(sm0[1][k]); }
         Part<T> tot[5];
         block_part<T, 5>(acc, red, tot);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 5; ++k) P[k * G + blockIdx.x] = tot[k];
+        if (!grid_reduce_sync<T, 5>(a.bar, tot, P, P + 5 * G, sh, red)) return;
     }
-    if (!grid_sync(a.bar)) return;
-    zl_gather<T, 5>(P, stepi, sh);
-    ++stepi;
     if (threadIdx.x == 0) {
         // the tests of every iteration in the working precision; double only for Newton steps
         const T res2 = part_to_T(sh[0], T()) * a.t_inv_n2;        // (eta * residual)^2
@@ -525,13 +500,7 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         for (int k = 0; k < 2; ++k) { ac2[k].add(sm1[0][k]); ac2[k].add(sm1[1][k]); }
         Part<T> t2[2];
         block_part<T, 2>(ac2, red, t2);
-        if (threadIdx.x == 0) {
-            P[(stepi & 1) * 5 * G + 0 * G + blockIdx.x] = t2[0];
-            P[(stepi & 1) * 5 * G + 1 * G + blockIdx.x] = t2[1];
-        }
-        if (!grid_sync(a.bar)) return;
-        zl_gather<T, 2>(P, stepi, sh);
-        ++stepi;
+        if (!grid_reduce_sync<T, 2>(a.bar, t2, P, P + 5 * G, sh, red)) return;
         if (threadIdx.x == 0) {
             const bool more = newton_update(ns, part_to_double(sh[0]), part_to_double(sh[1]));
             s_lam = ns.lam;

@@ -222,4 +222,67 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
     return ok != 0;
 }
 
+// Grid barrier that also sums NQ per-block values.  Thread 0 of every block passes its
+// block's values in `mine`; the last block to arrive sums the G blocks' values with all its
+// threads, block b's value at index b and the per-thread partial sums combined in a fixed
+// tree, so the totals do not depend on which block came last, writes them to `tot`
+// (global, NQ entries) and only then releases the others.  Every block leaves with the
+// totals in `sh` (shared, NQ entries).  One round trip of the slowest block instead of a
+// barrier followed by a gather in every block.  The spin of the waiting blocks is bounded
+// as in grid_sync; on a timeout the function returns false in every waiting block.
+template <typename T, int NQ>
+__device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* tot,
+                                                 Part<T>* sh, double* scratch) {
+    __shared__ int s_last, s_ok;
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const unsigned my_gen = *gb.gen;         // read before arriving
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) P[q * G + blockIdx.x] = mine[q];
+        __threadfence();
+        const unsigned arrived = atomicAdd(gb.count, 1u);
+        s_last = (arrived == (unsigned)G - 1u);
+        if (!s_last) {
+            const long long t0 = clock64();
+            while (*gb.gen == my_gen) {
+                if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
+                    atomicCAS(gb.err, 0, 5);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        Acc<T> a[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            Part<T> x;
+            part_zero(x);
+            for (int b = threadIdx.x; b < G; b += blockDim.x) x = part_add(x, part_ldcg(&P[q * G + b]));
+            a[q].v = x;
+        }
+        Part<T> t[NQ];
+        block_part<T, NQ>(a, scratch, t);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) { tot[q] = t[q]; sh[q] = t[q]; }
+            __threadfence();
+            *gb.count = 0u;
+            __threadfence();
+            atomicAdd((unsigned*)gb.gen, 1u);
+        }
+    } else if (threadIdx.x == 0 && s_ok) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q] = part_ldcg(&tot[q]);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 }  // namespace lbtr
