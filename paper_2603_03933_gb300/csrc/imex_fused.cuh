@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         for (int k = 0; k < 5; ++k) { acc[k].add(sm0[0][k]); acc[k].add(sm0[1][k]); }
         Part<T> tot[5];
         block_part<T, 5>(acc, red, tot);
-        if (!grid_reduce_sync<T, 5>(a.bar, tot, P, P + 5 * G, sh, red)) return;
+        if (!grid_reduce_sync<T, 5>(a.bar, tot, P, P + 5 * G, P + 5 * G + 5 * 64, sh)) return;
     }
     if (threadIdx.x == 0) {
         // the tests of every iteration in the working precision; double only for Newton steps
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
         for (int k = 0; k < 2; ++k) { ac2[k].add(sm1[0][k]); ac2[k].add(sm1[1][k]); }
         Part<T> t2[2];
         block_part<T, 2>(ac2, red, t2);
-        if (!grid_reduce_sync<T, 2>(a.bar, t2, P, P + 5 * G, sh, red)) return;
+        if (!grid_reduce_sync<T, 2>(a.bar, t2, P, P + 5 * G, P + 5 * G + 5 * 64, sh)) return;
         if (threadIdx.x == 0) {
             const bool more = newton_update(ns, part_to_double(sh[0]), part_to_double(sh[1]));
             s_lam = ns.lam;

@@ -191,6 +191,7 @@ struct GridBar {
     volatile unsigned* gen;
     int* err;
     long long budget;
+    unsigned* tree;          // grid_reduce_sync: [0] groups done, [1..64] arrivals per group
 };
 
 __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
@@ -222,64 +223,89 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
     return ok != 0;
 }
 
-// Grid barrier that also sums NQ per-block values.  Thread 0 of every block passes its
-// block's values in `mine`; the last block to arrive sums the G blocks' values with all its
-// threads, block b's value at index b and the per-thread partial sums combined in a fixed
-// tree, so the totals do not depend on which block came last, writes them to `tot`
-// (global, NQ entries) and only then releases the others.  Every block leaves with the
-// totals in `sh` (shared, NQ entries).  One round trip of the slowest block instead of a
-// barrier followed by a gather in every block.  The spin of the waiting blocks is bounded
-// as in grid_sync; on a timeout the function returns false in every waiting block.
+// Grid barrier that also sums NQ per-block values over a two-level tree.  Thread 0 of every
+// block passes its block's values in `mine`.  Blocks form groups of 32 consecutive blocks;
+// the last block of a group to arrive sums the group's values with one warp (one coalesced
+// load per quantity, a fixed shuffle tree), and the last group to finish sums the group
+// totals the same way, writes the totals to `tot` and releases the others.  Summation
+// order depends only on block indices, so results do not depend on arrival order.  Every
+// block leaves with the totals in `sh` (shared, NQ entries).  Storage: P [NQ][gridDim],
+// Q [NQ][64] group totals (grids of at most 2048 blocks), tot [NQ]; gb.tree holds the
+// group-completion counter and one arrival counter per group, all zero between barriers.
+// The spin of the waiting blocks is bounded as in grid_sync.
 template <typename T, int NQ>
-__device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* tot,
-                                                 Part<T>* sh, double* scratch) {
-    __shared__ int s_last, s_ok;
-    const int G = gridDim.x;
+__device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* Q,
+                                                 Part<T>* tot, Part<T>* sh) {
+    __shared__ int s_role, s_ok;               // 0: wait, 1: sums its group, 2: sums the groups
+    const int G = gridDim.x, blk = blockIdx.x, grp = blk >> 5;
+    const int gsize = (G - (grp << 5)) < 32 ? (G - (grp << 5)) : 32, ng = (G + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    unsigned my_gen = 0;
     if (threadIdx.x == 0) {
         s_ok = 1;
-        const unsigned my_gen = *gb.gen;         // read before arriving
+        s_role = 0;
+        my_gen = *gb.gen;                       // read before arriving
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) P[q * G + blockIdx.x] = mine[q];
+        for (int q = 0; q < NQ; ++q) P[q * G + blk] = mine[q];
         __threadfence();
-        const unsigned arrived = atomicAdd(gb.count, 1u);
-        s_last = (arrived == (unsigned)G - 1u);
-        if (!s_last) {
-            const long long t0 = clock64();
-            while (*gb.gen == my_gen) {
-                if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
-                    atomicCAS(gb.err, 0, 5);
-                    s_ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
+        if (atomicAdd(&gb.tree[1 + grp], 1u) == (unsigned)gsize - 1u) s_role = 1;
+    }
+    __syncthreads();
+    if (s_role >= 1 && threadIdx.x < 32) {
+        __threadfence();
+        Part<T> x[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (lane < gsize) x[q] = part_ldcg(&P[q * G + (grp << 5) + lane]);
+            else part_zero(x[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) x[q] = part_add(x[q], part_shfl_down(x[q], off));
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) Q[q * 64 + grp] = x[q];
+            gb.tree[1 + grp] = 0u;
             __threadfence();
+            if (atomicAdd(&gb.tree[0], 1u) == (unsigned)ng - 1u) s_role = 2;
+        }
+        __syncwarp();
+        if (__shfl_sync(0xffffffffu, s_role, 0) == 2) {
+            __threadfence();
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                part_zero(x[q]);
+                for (int k = lane; k < ng; k += 32) x[q] = part_add(x[q], part_ldcg(&Q[q * 64 + k]));
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) x[q] = part_add(x[q], part_shfl_down(x[q], off));
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) { tot[q] = x[q]; sh[q] = x[q]; }
+                gb.tree[0] = 0u;
+                __threadfence();
+                atomicAdd((unsigned*)gb.gen, 1u);
+            }
         }
     }
     __syncthreads();
-    if (s_last) {
+    if (s_role != 2 && threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (*gb.gen == my_gen) {
+            if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
+                atomicCAS(gb.err, 0, 5);
+                s_ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
         __threadfence();
-        Acc<T> a[NQ];
+        if (s_ok)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            Part<T> x;
-            part_zero(x);
-            for (int b = threadIdx.x; b < G; b += blockDim.x) x = part_add(x, part_ldcg(&P[q * G + b]));
-            a[q].v = x;
-        }
-        Part<T> t[NQ];
-        block_part<T, NQ>(a, scratch, t);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) { tot[q] = t[q]; sh[q] = t[q]; }
-            __threadfence();
-            *gb.count = 0u;
-            __threadfence();
-            atomicAdd((unsigned*)gb.gen, 1u);
-        }
-    } else if (threadIdx.x == 0 && s_ok) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) sh[q] = part_ldcg(&tot[q]);
+            for (int q = 0; q < NQ; ++q) sh[q] = part_ldcg(&tot[q]);
     }
     __syncthreads();
     return s_ok != 0;
