@@ -152,7 +152,10 @@ private:
     double* d_result_ = nullptr;     // [S_COUNT][SLOT_Q]
     unsigned* d_ticket_ = nullptr;   // [S_COUNT]
     double* d_secpart_ = nullptr;    // [2][3][coop_blocks]
-    unsigned* d_bar_ = nullptr;      // [2]: count, generation
+    // barrier words, one 128-byte line each: [0] count, [32] generation, [64] groups done,
+    // [64 + 32 (1 + g)] arrivals of group g (g < 64)
+    static constexpr int BAR_WORDS = 64 + 32 * 65;
+    unsigned* d_bar_ = nullptr;
     int* d_err_ = nullptr;
     ImexState* d_state_ = nullptr;
     int max_blocks_ = 0;

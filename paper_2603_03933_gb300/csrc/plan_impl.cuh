@@ -243,7 +243,7 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     size_t o_r = take(sizeof(double) * S_COUNT * SLOT_Q);
     size_t o_t = take(sizeof(unsigned) * S_COUNT);
     size_t o_sp = take(sizeof(double) * (2 * 5 * (size_t)std::max(coop_blocks_, zf_grid_) + 5 * 64 + 8));
-    size_t o_bar = take(sizeof(unsigned) * (2 + 65));
+    size_t o_bar = take(sizeof(unsigned) * BAR_WORDS);
     size_t o_err = take(sizeof(int));
     size_t o_st = take(sizeof(ImexState));
     bytes_ = off;
@@ -560,7 +560,7 @@ template <typename T> void Plan<T>::secular(const C* b, int check, int j, cudaSt
     a.res = slot(S_IMEX);
     a.st = d_state_;
     a.partials = d_secpart_;
-    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 1; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 2;
+    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 32; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 64;
     a.dim = dim_; a.m = m_; a.rows = rows_;
     a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
     a.eta = eta; a.r = r_; a.rtol = rtol_; a.steptol = steptol_;
@@ -592,7 +592,7 @@ template <typename T> void Plan<T>::zfused(const C* bold, C* bnew, int check, cu
     a.dim = dim_; a.m = m_;
     a.st = d_state_;
     a.partials = d_secpart_;
-    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 1; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 2;
+    a.bar.count = d_bar_; a.bar.gen = d_bar_ + 32; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 64;
     a.xi2 = (T)xi2_; a.eta = (T)eta;
     a.inv_n = 1.0 / (double)n_; a.inv_n2 = 1.0 / ((double)n_ * (double)n_);
     a.r = r_; a.rtol = rtol_; a.steptol = steptol_; a.eps_abs = eps_abs_; a.eps_rel_abs = eps_rel_abs_;
@@ -751,7 +751,7 @@ template <typename T> int Plan<T>::read_error(cudaStream_t s) {
 }
 
 template <typename T> void Plan<T>::reset_barrier(cudaStream_t s) {
-    cudaMemsetAsync(d_bar_, 0, (2 + 65) * sizeof(unsigned), s);
+    cudaMemsetAsync(d_bar_, 0, BAR_WORDS * sizeof(unsigned), s);
     cudaMemsetAsync(d_err_, 0, sizeof(int), s);
     cudaStreamSynchronize(s);
 }

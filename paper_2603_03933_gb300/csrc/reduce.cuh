@@ -191,7 +191,8 @@ struct GridBar {
     volatile unsigned* gen;
     int* err;
     long long budget;
-    unsigned* tree;          // grid_reduce_sync: [0] groups done, [1..64] arrivals per group
+    unsigned* tree;          // grid_reduce_sync: [0] groups done, [32 (1 + g)] arrivals of group g
+                             // (every counter on its own 128-byte line, apart from gen)
 };
 
 __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
@@ -231,7 +232,8 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
 // order depends only on block indices, so results do not depend on arrival order.  Every
 // block leaves with the totals in `sh` (shared, NQ entries).  Storage: P [NQ][gridDim],
 // Q [NQ][64] group totals (grids of at most 2048 blocks), tot [NQ]; gb.tree holds the
-// group-completion counter and one arrival counter per group, all zero between barriers.
+// group-completion counter and one arrival counter per group (each on its own 128-byte
+// line, away from gen, which every waiting block polls), all zero between barriers.
 // The spin of the waiting blocks is bounded as in grid_sync.
 template <typename T, int NQ>
 __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* Q,
@@ -248,7 +250,7 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
 #pragma unroll
         for (int q = 0; q < NQ; ++q) P[q * G + blk] = mine[q];
         __threadfence();
-        if (atomicAdd(&gb.tree[1 + grp], 1u) == (unsigned)gsize - 1u) s_role = 1;
+        if (atomicAdd(&gb.tree[32 * (1 + grp)], 1u) == (unsigned)gsize - 1u) s_role = 1;
     }
     __syncthreads();
     if (s_role >= 1 && threadIdx.x < 32) {
@@ -266,7 +268,7 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Q[q * 64 + grp] = x[q];
-            gb.tree[1 + grp] = 0u;
+            gb.tree[32 * (1 + grp)] = 0u;
             __threadfence();
             if (atomicAdd(&gb.tree[0], 1u) == (unsigned)ng - 1u) s_role = 2;
         }
@@ -294,13 +296,15 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
     __syncthreads();
     if (s_role != 2 && threadIdx.x == 0) {
         const long long t0 = clock64();
+        unsigned ns = 32;
         while (*gb.gen == my_gen) {
             if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
                 atomicCAS(gb.err, 0, 5);
                 s_ok = 0;
                 break;
             }
-            __nanosleep(32);
+            __nanosleep(ns);               // back off: fewer polls of gen while the tree works
+            if (ns < 256) ns *= 2;
         }
         __threadfence();
         if (s_ok)
