@@ -413,7 +413,6 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
             sm0[m & 1][2] += ci * ra * ra;
             sm0[m & 1][3] += qv;
             sm0[m & 1][4] += (T)-2 * eta * qv * rd;
-            a.bnew[base + (long long)e * es] = x;
         }
     }
     Part<T>* P = reinterpret_cast<Part<T>*>(a.partials);
@@ -512,6 +511,13 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->lam = s_lam;
         st->newton += ns.newton;
+    }
+
+    // b_j for the next iteration's residual, stored only now: a grid barrier's fence waits
+    // for a block's outstanding stores, and nothing in this launch reads b_j back
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < L1; ++m) a.bnew[base + (long long)fo(m) * es] = v[m];
     }
 
     // 4. the implicit diagonal solve and the inverse transform of the columns
