@@ -275,10 +275,21 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
         __syncwarp();
         if (__shfl_sync(0xffffffffu, s_role, 0) == 2) {
             __threadfence();
+            // groups 0..31: one independent load per lane and quantity, all in flight together
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                part_zero(x[q]);
-                for (int k = lane; k < ng; k += 32) x[q] = part_add(x[q], part_ldcg(&Q[q * 64 + k]));
+                if (lane < ng) x[q] = part_ldcg(&Q[q * 64 + lane]);
+                else part_zero(x[q]);
+            }
+            if (ng > 32) {
+                Part<T> y[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    if (lane + 32 < ng) y[q] = part_ldcg(&Q[q * 64 + 32 + lane]);
+                    else part_zero(y[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) x[q] = part_add(x[q], y[q]);
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
