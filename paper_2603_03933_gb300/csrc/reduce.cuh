@@ -235,6 +235,21 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
 // group-completion counter and one arrival counter per group (each on its own 128-byte
 // line, away from gen, which every waiting block polls), all zero between barriers.
 // The spin of the waiting blocks is bounded as in grid_sync.
+// GPU-scope atomics and loads with acquire / release semantics (PTX memory model)
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 template <typename T, int NQ>
 __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* Q,
                                                  Part<T>* tot, Part<T>* sh) {
@@ -242,19 +257,19 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
     const int G = gridDim.x, blk = blockIdx.x, grp = blk >> 5;
     const int gsize = (G - (grp << 5)) < 32 ? (G - (grp << 5)) : 32, ng = (G + 31) >> 5;
     const int lane = threadIdx.x & 31;
+    unsigned* gen = (unsigned*)gb.gen;
     unsigned my_gen = 0;
     if (threadIdx.x == 0) {
         s_ok = 1;
         s_role = 0;
-        my_gen = *gb.gen;                       // read before arriving
+        my_gen = ld_acquire_gpu(gen);            // read before arriving
 #pragma unroll
         for (int q = 0; q < NQ; ++q) P[q * G + blk] = mine[q];
-        __threadfence();
-        if (atomicAdd(&gb.tree[32 * (1 + grp)], 1u) == (unsigned)gsize - 1u) s_role = 1;
+        // release: this block's values before its arrival; acquire: the group's values for its last
+        if (atom_add_acq_rel_gpu(&gb.tree[32 * (1 + grp)], 1u) == (unsigned)gsize - 1u) s_role = 1;
     }
     __syncthreads();
     if (s_role >= 1 && threadIdx.x < 32) {
-        __threadfence();
         Part<T> x[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -269,12 +284,10 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Q[q * 64 + grp] = x[q];
             gb.tree[32 * (1 + grp)] = 0u;
-            __threadfence();
-            if (atomicAdd(&gb.tree[0], 1u) == (unsigned)ng - 1u) s_role = 2;
+            if (atom_add_acq_rel_gpu(&gb.tree[0], 1u) == (unsigned)ng - 1u) s_role = 2;
         }
         __syncwarp();
         if (__shfl_sync(0xffffffffu, s_role, 0) == 2) {
-            __threadfence();
             // groups 0..31: one independent load per lane and quantity, all in flight together
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -299,8 +312,7 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) { tot[q] = x[q]; sh[q] = x[q]; }
                 gb.tree[0] = 0u;
-                __threadfence();
-                atomicAdd((unsigned*)gb.gen, 1u);
+                red_add_release_gpu(gen, 1u);        // totals and counter resets before the release
             }
         }
     }
@@ -308,7 +320,7 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
     if (s_role != 2 && threadIdx.x == 0) {
         const long long t0 = clock64();
         unsigned ns = 32;
-        while (*gb.gen == my_gen) {
+        while (ld_acquire_gpu(gen) == my_gen) {
             if (*(volatile int*)gb.err != 0 || clock64() - t0 > gb.budget) {
                 atomicCAS(gb.err, 0, 5);
                 s_ok = 0;
@@ -317,7 +329,6 @@ __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T
             __nanosleep(ns);               // back off: fewer polls of gen while the tree works
             if (ns < 256) ns *= 2;
         }
-        __threadfence();
         if (s_ok)
 #pragma unroll
             for (int q = 0; q < NQ; ++q) sh[q] = part_ldcg(&tot[q]);
