@@ -141,6 +141,21 @@ __device__ __forceinline__ double block_max(double v, double* scratch) {
     return m;
 }
 
+// GPU-scope atomics and loads with acquire / release semantics (PTX memory model)
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Partial-sum bookkeeping of one reduction launch.
 struct RedSlot {
     double* partials;    // [nq][gridDim.x]
@@ -154,23 +169,27 @@ struct RedSlot {
 // The last block to arrive combines all partials in index order and resets the ticket.
 __device__ __forceinline__ void finalize_partials(const RedSlot& rs, const double* vals) {
     __shared__ int am_last;
+    const unsigned G = gridDim.x;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < rs.nq; ++q) rs.partials[q * gridDim.x + blockIdx.x] = vals[q];
-        __threadfence();
-        unsigned t = atomicAdd(rs.ticket, 1u);
-        am_last = (t == gridDim.x - 1);
+        for (int q = 0; q < rs.nq; ++q) rs.partials[q * G + blockIdx.x] = vals[q];
+        // release: this block's partials before its ticket; acquire: all partials for the last
+        am_last = (atom_add_acq_rel_gpu(rs.ticket, 1u) == G - 1u);
     }
     __syncthreads();
     if (am_last) {
-        __threadfence();
         for (int q = threadIdx.x >> 5; q < rs.nq; q += (blockDim.x >> 5) > 0 ? (blockDim.x >> 5) : 1) {
-            // one warp per quantity; fixed order within the warp: deterministic
+            // one warp per quantity; lane l sums blocks l, l + 32, ... in that order (deterministic);
+            // the loads of a batch of 8 are independent, so they are in flight together
             const int lane = threadIdx.x & 31;
             const bool is_max = (rs.max_mask >> q) & 1u;
-            double s = is_max ? 0.0 : 0.0;
-            for (unsigned b = lane; b < gridDim.x; b += 32) {
-                double x = ((volatile double*)rs.partials)[q * gridDim.x + b];
-                s = is_max ? fmax(s, x) : s + x;
+            double s = 0.0;
+            for (unsigned b0 = lane; b0 < G; b0 += 256) {
+                double x[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = (b0 + 32 * j < G) ? __ldcg(&rs.partials[q * G + b0 + 32 * j]) : 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (b0 + 32 * j < G) s = is_max ? fmax(s, x[j]) : s + x[j];
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -235,21 +254,6 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
 // group-completion counter and one arrival counter per group (each on its own 128-byte
 // line, away from gen, which every waiting block polls), all zero between barriers.
 // The spin of the waiting blocks is bounded as in grid_sync.
-// GPU-scope atomics and loads with acquire / release semantics (PTX memory model)
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename T, int NQ>
 __device__ __forceinline__ bool grid_reduce_sync(const GridBar& gb, const Part<T>* mine, Part<T>* P, Part<T>* Q,
                                                  Part<T>* tot, Part<T>* sh) {
