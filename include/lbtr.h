@@ -209,6 +209,12 @@ typedef struct {
     lb_eig_opts eig;     /* lambda_min options for the second-order test */
     int pcg_max_iter;    /* cap on CG iterations of each CONTRACT linear solve */
     double pcg_rtol;     /* relative tolerance of those solves */
+    /* Nearly hard subproblems (§4.4 and the remark on the hard case after the global-
+     * optimality theorem): if hard_tol > 0, every outer iteration computes lambda_min(H)
+     * and its Ritz vector u (Lanczos, options `eig`); when lambda_min < 0 and
+     * |<g, u>_N| <= hard_tol (the component g^(1) of g along u), the subproblem starts
+     * from a random point of the trust region instead of -r g / ||g||.  0: off. */
+    double hard_tol;
 } lb_tr_opts;
 
 typedef struct {
@@ -219,6 +225,8 @@ typedef struct {
     double gmax;         /* max_x |g| at the returned iterate */
     double lambda_min;   /* last second-order test value (NaN if never run) */
     int status;          /* lb_status of the solve */
+    int randomized;      /* subproblems started from a random point of the ball */
+    double g1_min;       /* smallest |g^(1)| seen by the nearly-hard test (NaN if never run) */
 } lb_tr_info;
 
 void lb_default_tr_opts(lb_tr_opts *o);

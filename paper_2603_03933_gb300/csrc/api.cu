@@ -69,6 +69,7 @@ void lb_default_tr_opts(lb_tr_opts* o) {
     lb_default_eig_opts(&o->eig);
     o->pcg_max_iter = 2000;
     o->pcg_rtol = 1e-10;
+    o->hard_tol = 0.0;
 }
 
 lb_status lb_create(const lb_problem* prob, lb_precision prec, lb_ctx** out) {
@@ -230,6 +231,7 @@ lb_status lb_imex_tr_solve(lb_ctx* ctx, double* phi_inout, const lb_tr_opts* opt
     lb_tr_info inf;
     std::memset(&inf, 0, sizeof(inf));
     inf.lambda_min = std::numeric_limits<double>::quiet_NaN();
+    inf.g1_min = std::numeric_limits<double>::quiet_NaN();
     lb_status st = ctx->tr_solve(phi_inout, o, &inf, (cudaStream_t)stream);
     inf.status = (int)st;
     if (info) *info = inf;

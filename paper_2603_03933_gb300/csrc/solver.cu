@@ -301,6 +301,22 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
             if (ei.lambda_min >= -o.tol2) { result = LB_OK; break; }
             random_next = true;   // a saddle: leave it from a random point of the ball
         }
+        if (o.hard_tol > 0.0 && !random_next) {
+            // the nearly hard case: g (almost) orthogonal to the eigenvector of a negative
+            // lambda_min, which the deterministic start -r g / ||g|| can then never reach
+            double* u = f64[7];
+            lb_eig_info ei;
+            std::memset(&ei, 0, sizeof(ei));
+            lb_status es = lambda_min<double>(P, v, o.eig, u, &ei, s);
+            if (es != LB_OK && es != LB_ERR_NOCONV) return es;
+            double gu = 0.0, uu = 0.0;
+            if ((st = dot<double>(P, g, u, &gu, s))) return st;
+            if ((st = dot<double>(P, u, u, &uu, s))) return st;
+            const double g1 = std::fabs(gu) / std::sqrt(std::max(uu, 1e-300));
+            info->lambda_min = ei.lambda_min;
+            if (!(g1 >= info->g1_min)) info->g1_min = g1;
+            if (ei.lambda_min < 0.0 && g1 <= o.hard_tol) random_next = true;
+        }
         // ---- subproblem (Algorithm 3) in the working precision ----
         lb_sub_info si;
         std::memset(&si, 0, sizeof(si));
@@ -330,6 +346,7 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
             ss = subproblem<float>(Q, v32, g32, S.r, d0, so, d32, &si, s);
             k_convert<double, float><<<grid, 256, 0, s>>>(sd, d32, P.n());
         }
+        if (random_next) ++info->randomized;
         random_next = false;
         if (ss != LB_OK && ss != LB_ERR_NOCONV) return ss;
         info->inner += si.iterations;

@@ -62,13 +62,14 @@ class lb_tr_opts(ctypes.Structure):
                 ("mu0", ctypes.c_double), ("r0", ctypes.c_double), ("nu0", ctypes.c_double),
                 ("eps", ctypes.c_double), ("max_outer", ctypes.c_int), ("second_order", ctypes.c_int),
                 ("tol2", ctypes.c_double), ("sub", lb_sub_opts), ("eig", lb_eig_opts),
-                ("pcg_max_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double)]
+                ("pcg_max_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("hard_tol", ctypes.c_double)]
 
 
 class lb_tr_info(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("inner", ctypes.c_longlong), ("accepted", ctypes.c_int),
                 ("contracted", ctypes.c_int), ("shrunk", ctypes.c_int), ("energy", ctypes.c_double),
-                ("gmax", ctypes.c_double), ("lambda_min", ctypes.c_double), ("status", ctypes.c_int)]
+                ("gmax", ctypes.c_double), ("lambda_min", ctypes.c_double), ("status", ctypes.c_int),
+                ("randomized", ctypes.c_int), ("g1_min", ctypes.c_double)]
 
 
 # (name, restype, argtypes) of every exported entry point declared in include/lbtr.h
@@ -307,7 +308,8 @@ def lb_imex_tr_solve(ctx: Context, phi64, opts: lb_tr_opts | None = None, stream
         _check(ctx, st, "lb_imex_tr_solve")
     return {"outer": info.outer, "inner": info.inner, "accepted": info.accepted, "contracted": info.contracted,
             "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
-            "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": st}
+            "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": st,
+            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None}
 
 
 def lb_set_barrier_budget(ctx: Context, cycles: int):
