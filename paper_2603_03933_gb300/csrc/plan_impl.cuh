@@ -6,6 +6,7 @@
 #include "plan.cuh"
 #include "planes.cuh"
 #include "lines.cuh"
+#include "rows.cuh"
 #include "imex_fused.cuh"
 
 namespace lbtr {
@@ -29,14 +30,19 @@ namespace lbtr {
         default: break;                                             \
     }
 
+// x rows: the four-step row kernels for M >= 16, the shared-memory Stockham kernels for M = 8
+template <typename T, int M> int rows_grid(int rows) { return (rows + RowGeo<M>::NR - 1) / RowGeo<M>::NR; }
 template <typename T, int M, int MODE> void launch_xfwd(const XfArgs<T>& a, int grid, cudaStream_t s) {
-    k_xfwd<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+    if constexpr (M >= 16) k_rows_fwd<T, M, MODE><<<rows_grid<T, M>(a.rows), 128, rows_smem<T, M>(), s>>>(a);
+    else k_xfwd<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
 }
 template <typename T, int M, int MODE> void launch_xinv(const XiArgs<T>& a, int grid, cudaStream_t s) {
-    k_xinv<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+    if constexpr (M >= 16) k_rows_inv<T, M, MODE><<<rows_grid<T, M>(a.rows), 128, rows_smem<T, M>(), s>>>(a);
+    else k_xinv<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
 }
 template <typename T, int M, int MODE> void launch_xmid(const XmArgs<T>& a, int grid, cudaStream_t s) {
-    k_xmid<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
+    if constexpr (M >= 16) k_rows_mid<T, M, MODE><<<rows_grid<T, M>(a.rows), 128, rows_smem<T, M>(), s>>>(a);
+    else k_xmid<T, M, MODE><<<grid, x_nt(M), x_smem<T>(M), s>>>(a);
 }
 template <typename T, int M, int MODE> void launch_cols(const ColArgs<T>& a, int grid, cudaStream_t s) {
     k_cols<T, M, MODE><<<grid, col_nt(M), col_smem<T>(M), s>>>(a);
@@ -125,6 +131,21 @@ template <typename T, int M> cudaError_t set_smem_attrs() {
     setx((const void*)k_xinv<T, M, XI_GRAD>);
     setx((const void*)k_xmid<T, M, XM_IMEX>);
     setx((const void*)k_xmid<T, M, XM_TOP>);
+    if constexpr (M >= 16) {
+        auto setr = [&](const void* f) {
+            cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem<T, M>());
+            if (r != cudaSuccess) e = r;
+        };
+        setr((const void*)k_rows_fwd<T, M, XF_PLAIN>);
+        setr((const void*)k_rows_fwd<T, M, XF_HVPMEAN>);
+        setr((const void*)k_rows_fwd<T, M, XF_ENERGY>);
+        setr((const void*)k_rows_fwd<T, M, XF_IMEX0>);
+        setr((const void*)k_rows_inv<T, M, XI_PLAIN>);
+        setr((const void*)k_rows_inv<T, M, XI_HVP>);
+        setr((const void*)k_rows_inv<T, M, XI_GRAD>);
+        setr((const void*)k_rows_mid<T, M, XM_IMEX>);
+        setr((const void*)k_rows_mid<T, M, XM_TOP>);
+    }
     setc((const void*)k_cols<T, M, C_FWD>);
     setc((const void*)k_cols<T, M, C_INV>);
     setc((const void*)k_cols<T, M, C_LAM>);
