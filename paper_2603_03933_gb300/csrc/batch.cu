@@ -1,13 +1,15 @@
 // Batches of independent problems (the phase-diagram sweep): one context per problem and
 // the Hessian-vector products of all of them recorded as one CUDA graph.
 //
-// The graph forks from a private capture stream into up to 16 side streams; problems are
-// placed largest first on the side stream with the least work so far (a longest-first
-// list schedule, the static work queue of the batch), each as the three launches of its
-// own hessvec.  Branches on different side streams share no data and no scratch, so the
-// GPU runs them concurrently; the small grids of small problems fill the SMs together.
-// The graph is recorded on the first call with a given set of field pointers and
-// replayed by later calls with the same pointers.
+// Problems on the x-row path (2D grids, 3D grids above 128^3) are grouped by grid size and
+// precision; each group runs as three launches (rows forward, innermost lines, rows
+// inverse) whose blockIdx.y selects a problem's argument struct from a device array, so a
+// sweep of hundreds of small problems is a dozen launches instead of three per problem.
+// Other problems (3D plane path) are separate branches.  Branches fork from a private
+// capture stream into up to 16 side streams, largest first onto the least-loaded stream
+// (a longest-first list schedule); they share no data and no scratch (one context each),
+// so the GPU runs them side by side.  The graph is recorded on the first call with a given
+// set of field pointers and replayed by later calls with the same pointers.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -15,8 +17,15 @@
 
 #include "ctx.cuh"
 
+struct BatchGroup {                         // problems of one size on the x-row path
+    int m = 0, rows = 0, col_grid = 0, col_tiles = 0;
+    std::vector<int> members;
+    void* args = nullptr;                     // device: [count] XfArgs, [count] ColArgs, [count] XiArgs
+};
+
 struct lb_batch {
     std::vector<lb_ctx*> ctx;
+    std::vector<BatchGroup> groups;
     std::vector<int> order;                 // problems, largest first
     std::vector<int> lane;                  // side stream of each problem
     int nstreams = 0;
@@ -29,7 +38,12 @@ struct lb_batch {
     std::vector<const void*> key;           // the pointers the graph was recorded with
     std::string err;
 
+    void free_groups() {
+        for (BatchGroup& g : groups) if (g.args) cudaFree(g.args);
+        groups.clear();
+    }
     ~lb_batch() {
+        free_groups();
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
@@ -50,6 +64,73 @@ lb_status batch_cuda(lb_batch* b, cudaError_t e, const char* where) {
     return batch_fail(b, LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 }  // namespace
+
+// Group the problems on the x-row path by (precision, dimension, size) and upload each
+// group's argument structs (they hold the field pointers of this call).
+template <typename T>
+static lb_status upload_group(lb_batch* b, BatchGroup& g, const void* const* phi, const void* const* v,
+                              void* const* hv) {
+    const int cnt = (int)g.members.size();
+    std::vector<lbtr::XfArgs<T>> xf(cnt);
+    std::vector<lbtr::ColArgs<T>> ca(cnt);
+    std::vector<lbtr::XiArgs<T>> xi(cnt);
+    for (int q = 0; q < cnt; ++q) {
+        const int i = g.members[q];
+        lbtr::Plan<T>* p = sizeof(T) == 8 ? reinterpret_cast<lbtr::Plan<T>*>(b->ctx[i]->p64)
+                                          : reinterpret_cast<lbtr::Plan<T>*>(b->ctx[i]->p32);
+        int cg = 0, ct = 0;
+        p->hvp_args((const T*)phi[i], (const T*)v[i], (T*)hv[i], xf[q], ca[q], cg, ct, xi[q]);
+    }
+    const size_t bytes = cnt * (sizeof(lbtr::XfArgs<T>) + sizeof(lbtr::ColArgs<T>) + sizeof(lbtr::XiArgs<T>));
+    lb_status st = batch_cuda(b, cudaMalloc(&g.args, bytes), "lb_batch_hessvec/arguments");
+    if (st) { g.args = nullptr; return st; }
+    char* d = static_cast<char*>(g.args);
+    cudaMemcpy(d, xf.data(), cnt * sizeof(lbtr::XfArgs<T>), cudaMemcpyHostToDevice);
+    d += cnt * sizeof(lbtr::XfArgs<T>);
+    cudaMemcpy(d, ca.data(), cnt * sizeof(lbtr::ColArgs<T>), cudaMemcpyHostToDevice);
+    d += cnt * sizeof(lbtr::ColArgs<T>);
+    return batch_cuda(b, cudaMemcpy(d, xi.data(), cnt * sizeof(lbtr::XiArgs<T>), cudaMemcpyHostToDevice),
+                      "lb_batch_hessvec/arguments");
+}
+
+static lb_status record_groups(lb_batch* b, const void* const* phi, const void* const* v, void* const* hv) {
+    b->free_groups();
+    const int n = (int)b->ctx.size();
+    for (int i : b->order) {
+        lb_ctx* c = b->ctx[i];
+        int m = c->prob.n, rows = 0, cg = 0, ct = 0;
+        bool ok;
+        if (c->prec == LB_FP64) {
+            lbtr::XfArgs<double> xf; lbtr::ColArgs<double> ca; lbtr::XiArgs<double> xi;
+            ok = c->p64->hvp_args((const double*)phi[i], (const double*)v[i], (double*)hv[i], xf, ca, cg, ct, xi);
+            rows = xf.rows;
+        } else {
+            lbtr::XfArgs<float> xf; lbtr::ColArgs<float> ca; lbtr::XiArgs<float> xi;
+            ok = c->p32->hvp_args((const float*)phi[i], (const float*)v[i], (float*)hv[i], xf, ca, cg, ct, xi);
+            rows = xf.rows;
+        }
+        if (!ok) continue;
+        BatchGroup* g = nullptr;
+        for (BatchGroup& x : b->groups) {
+            lb_ctx* c0 = b->ctx[x.members[0]];
+            if (x.m == m && x.rows == rows && c0->prec == c->prec && c0->prob.dim == c->prob.dim &&
+                x.col_grid == cg && x.col_tiles == ct) { g = &x; break; }
+        }
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->m = m; g->rows = rows; g->col_grid = cg; g->col_tiles = ct;
+        }
+        g->members.push_back(i);
+    }
+    (void)n;
+    for (BatchGroup& g : b->groups) {
+        lb_status st = b->ctx[g.members[0]]->prec == LB_FP64 ? upload_group<double>(b, g, phi, v, hv)
+                                                             : upload_group<float>(b, g, phi, v, hv);
+        if (st) return st;
+    }
+    return LB_OK;
+}
 
 extern "C" {
 
@@ -122,14 +203,43 @@ lb_status lb_batch_hessvec(lb_batch* b, const void* const* phi, const void* cons
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
         b->key.clear();
+        if ((st = record_groups(b, phi, v, hv))) return st;
         if ((st = batch_cuda(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal),
                              "lb_batch_hessvec/capture")))
             return st;
         cudaEventRecord(b->fork, b->cap);
         for (int k = 0; k < b->nstreams; ++k) cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        std::vector<long long> load(b->nstreams, 0);
+        auto least = [&]() { return (int)(std::min_element(load.begin(), load.end()) - load.begin()); };
+        std::vector<char> grouped(n, 0);
+        cudaError_t le = cudaSuccess;
+        for (BatchGroup& g : b->groups) {
+            const int k = least();
+            const int cnt = (int)g.members.size();
+            long long pts = 0;
+            for (int i : g.members) { grouped[i] = 1; pts += b->ctx[i]->n(); }
+            load[k] += pts;
+            const lb_precision pr = b->ctx[g.members[0]]->prec;
+            cudaError_t e;
+            if (pr == LB_FP64) {
+                auto* xf = static_cast<lbtr::XfArgs<double>*>(g.args);
+                auto* ca = reinterpret_cast<lbtr::ColArgs<double>*>(xf + cnt);
+                auto* xi = reinterpret_cast<lbtr::XiArgs<double>*>(ca + cnt);
+                e = lbtr::launch_hvp_batch<double>(g.m, g.rows, cnt, xf, ca, g.col_grid, g.col_tiles, xi, b->side[k]);
+            } else {
+                auto* xf = static_cast<lbtr::XfArgs<float>*>(g.args);
+                auto* ca = reinterpret_cast<lbtr::ColArgs<float>*>(xf + cnt);
+                auto* xi = reinterpret_cast<lbtr::XiArgs<float>*>(ca + cnt);
+                e = lbtr::launch_hvp_batch<float>(g.m, g.rows, cnt, xf, ca, g.col_grid, g.col_tiles, xi, b->side[k]);
+            }
+            if (e != cudaSuccess && le == cudaSuccess) le = e;
+        }
         for (int i : b->order) {
+            if (grouped[i]) continue;
             lb_ctx* c = b->ctx[i];
-            cudaStream_t s = b->side[b->lane[i]];
+            const int k = least();
+            load[k] += c->n();
+            cudaStream_t s = b->side[k];
             if (c->prec == LB_FP64) c->p64->hessvec((const double*)phi[i], (const double*)v[i], (double*)hv[i], s);
             else c->p32->hessvec((const float*)phi[i], (const float*)v[i], (float*)hv[i], s);
         }
@@ -139,8 +249,8 @@ lb_status lb_batch_hessvec(lb_batch* b, const void* const* phi, const void* cons
         }
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b->cap, &g);
-        cudaError_t le = cudaGetLastError();
-        if (e == cudaSuccess) e = le;
+        cudaError_t le2 = cudaGetLastError();
+        if (e == cudaSuccess) e = le != cudaSuccess ? le : le2;
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return batch_cuda(b, e, "lb_batch_hessvec/record");

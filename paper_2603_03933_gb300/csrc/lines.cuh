@@ -28,7 +28,7 @@ __host__ __device__ constexpr bool ln_mode_ok(int mode) {
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(ln_nt(M)) k_lines(ColArgs<T> a, int ntiles) {
+__device__ __forceinline__ void lines_body(const ColArgs<T>& a, int ntiles) {
     constexpr int NL = LN_NL, L1 = fs_l1(M), L2 = fs_l2(M), RR = L1 / L2, TS = M + 1, H = M / 2;
     constexpr int HSH = (H >= 256) ? 8 : (H >= 128) ? 7 : (H >= 64) ? 6 : (H >= 32) ? 5 : (H >= 16) ? 4 : (H >= 8) ? 3 : 2;
     static_assert((1 << HSH) == H, "H must be a power of two");
@@ -158,6 +158,14 @@ __global__ void __launch_bounds__(ln_nt(M)) k_lines(ColArgs<T> a, int ntiles) {
         if (threadIdx.x == 0) tot[0] *= a.escale;
         finalize_partials(a.red, tot);
     }
+}
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(ln_nt(M)) k_lines(ColArgs<T> a, int ntiles) { lines_body<T, M, MODE>(a, ntiles); }
+// many problems of the same size per launch: blockIdx.y selects the problem's arguments
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(ln_nt(M)) k_lines_b(const ColArgs<T>* __restrict__ args, int ntiles) {
+    lines_body<T, M, MODE>(args[blockIdx.y], ntiles);
 }
 
 }  // namespace lbtr

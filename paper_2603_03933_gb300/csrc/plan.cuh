@@ -107,6 +107,12 @@ public:
 
     static constexpr long long kDefaultBudget = 4000000000LL;   // ~2 s at 2 GHz
 
+    // the argument structs of one hessvec on the x-row path (for batched launches); false elsewhere
+    bool hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid, int& col_tiles,
+                  XiArgs<T>& xi) const;
+    int col_args(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
+                 const double* lam, int slot, const int* done, ColArgs<T>& a) const;
+
 private:
     void xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
               C* spec, int slot, cudaStream_t s, const int* done = nullptr);
@@ -169,5 +175,11 @@ private:
     double fb() const { return (double)n_ * sizeof(T); }
     double sb() const { return (double)spec_len() * sizeof(C); }
 };
+
+// hessvec of `count` problems of grid size m on the x-row path in one launch per pass;
+// xf, ca, xi: device arrays of `count` argument structs from Plan<T>::hvp_args
+template <typename T>
+cudaError_t launch_hvp_batch(int m, int rows, int count, const XfArgs<T>* xf, const ColArgs<T>* ca, int col_grid,
+                             int col_tiles, const XiArgs<T>* xi, cudaStream_t s);
 
 }  // namespace lbtr

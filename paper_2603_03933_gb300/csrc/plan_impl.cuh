@@ -76,6 +76,7 @@ template <typename T, int M> cudaError_t set_lines_attrs(int* per) {
         setl((const void*)k_lines<T, M, C_LAM>);
         setl((const void*)k_lines<T, M, C_LAM_E>);
         setl((const void*)k_lines<T, M, C_SOLVE>);
+        setl((const void*)k_lines_b<T, M, C_LAM>);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_lines<T, M, C_LAM>, ln_nt(M), ln_smem<T>(M));
     }
@@ -145,6 +146,8 @@ template <typename T, int M> cudaError_t set_smem_attrs() {
         setr((const void*)k_rows_inv<T, M, XI_GRAD>);
         setr((const void*)k_rows_mid<T, M, XM_IMEX>);
         setr((const void*)k_rows_mid<T, M, XM_TOP>);
+        setr((const void*)k_rows_fwd_b<T, M, XF_HVPMEAN>);
+        setr((const void*)k_rows_inv_b<T, M, XI_HVP>);
     }
     setc((const void*)k_cols<T, M, C_FWD>);
     setc((const void*)k_cols<T, M, C_INV>);
@@ -383,9 +386,8 @@ void Plan<T>::xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStr
 
 // axis: 1 = Y, 2 = Z
 template <typename T>
-void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
-                   const double* lam, int slot, cudaStream_t s, const int* done) {
-    ColArgs<T> a;
+int Plan<T>::col_args(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
+                      const double* lam, int slot, const int* done, ColArgs<T>& a) const {
     const long long M = m_, H = h_;
     a.main = spec; a.nyq = spec ? spec + (size_t)rows_ * h_ : nullptr;
     a.dst_main = dst; a.dst_nyq = dst ? dst + (size_t)rows_ * h_ : nullptr;
@@ -408,8 +410,16 @@ void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, 
     int grid = a.nb_main + (s1.nlines + COL_NL - 1) / COL_NL;
     a.dim = dim_; a.xi2 = (T)xi2_; a.kscale = kscale; a.escale = escale; a.eta = (T)eta;
     a.sigma = (T)sigma; a.lam = lam;
-    a.red = redslot(slot, mode == C_IMEX_OUT ? 2 : mode == C_DBOX ? 3 : 1, 0u);
+    a.red = const_cast<Plan<T>*>(this)->redslot(slot, mode == C_IMEX_OUT ? 2 : mode == C_DBOX ? 3 : 1, 0u);
     a.done = done;
+    return grid;
+}
+
+template <typename T>
+void Plan<T>::cols(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
+                   const double* lam, int slot, cudaStream_t s, const int* done) {
+    ColArgs<T> a;
+    const int grid = col_args(axis, mode, spec, dst, src, kscale, escale, sigma, lam, slot, done, a);
     cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
     const bool lines = ln_grid_cap_ > 0 && ln_mode_ok(mode) && dst == nullptr && src == nullptr;
     if (lines) {
@@ -524,6 +534,53 @@ template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cud
     fwd_outer(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
     cols(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0, s);
     inv_outer(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
+}
+
+// The three argument structs of hessvec on the x-row path (2D grids and 3D grids above
+// 128^3), for batched launches of many problems of the same size; false on other paths.
+template <typename T>
+bool Plan<T>::hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid,
+                       int& col_tiles, XiArgs<T>& xi) const {
+    if (use_planes_ || m_ < 16 || ln_grid_cap_ <= 0) return false;
+    Plan<T>* self = const_cast<Plan<T>*>(this);
+    xf.in = v; xf.phi = phi; xf.g = nullptr; xf.d0 = nullptr; xf.dscale = nullptr;
+    xf.main = d_work_; xf.nyq = d_work_ + (size_t)rows_ * h_;
+    xf.tw = d_tw_; xf.rows = rows_; xf.model = model_; xf.model.eta = (T)eta;
+    xf.red = self->redslot(S_HVP, 1, 0u);
+    xf.done = nullptr;
+    const int inner = dim_ == 3 ? 2 : 1;
+    col_tiles = col_args(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0,
+                         nullptr, ca);
+    col_grid = std::min(col_tiles, ln_grid_cap_);
+    xi.main = d_work_; xi.nyq = d_work_ + (size_t)rows_ * h_;
+    xi.out = hv; xi.phi = phi; xi.v = v; xi.msum = self->slot(S_HVP); xi.inv_n = 1.0 / (double)n_;
+    xi.oscale = (T)1; xi.tw = d_tw_; xi.rows = rows_; xi.model = model_; xi.model.eta = (T)eta;
+    xi.red = self->redslot(S_RED0, 1, 1u);
+    xi.done = nullptr;
+    return true;
+}
+
+// hessvec of `count` problems of grid size m at once (device argument arrays from hvp_args)
+template <typename T>
+cudaError_t launch_hvp_batch(int m, int rows, int count, const XfArgs<T>* xf, const ColArgs<T>* ca, int col_grid,
+                             int col_tiles, const XiArgs<T>* xi, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    LB_SWITCH_M(m, {
+        if constexpr (M >= 16) {
+            const dim3 gx((unsigned)rows_grid<T, M>(rows), (unsigned)count);
+            k_rows_fwd_b<T, M, XF_HVPMEAN><<<gx, 128, rows_smem<T, M>(), s>>>(xf);
+            if constexpr (M <= 256) {
+                k_lines_b<T, M, C_LAM><<<dim3((unsigned)col_grid, (unsigned)count), ln_nt(M), ln_smem<T>(M), s>>>(ca, col_tiles);
+            } else {
+                e = cudaErrorInvalidValue;
+            }
+            k_rows_inv_b<T, M, XI_HVP><<<gx, 128, rows_smem<T, M>(), s>>>(xi);
+        } else {
+            e = cudaErrorInvalidValue;
+        }
+    });
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
 }
 
 template <typename T> void Plan<T>::energy_grad(const T* phi, T* grad, cudaStream_t s) {

@@ -168,7 +168,7 @@ template <int M> __device__ __forceinline__ long long rows_idx(long long row0, i
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(128) k_rows_fwd(XfArgs<T> a) {
+__device__ __forceinline__ void rows_fwd_body(const XfArgs<T>& a) {
     using G = RowGeo<M>;
     using C = cplx<T>;
     constexpr int L1 = G::L1;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(128) k_rows_fwd(XfArgs<T> a) {
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(128) k_rows_inv(XiArgs<T> a) {
+__device__ __forceinline__ void rows_inv_body(const XiArgs<T>& a) {
     using G = RowGeo<M>;
     using C = cplx<T>;
     constexpr int L1 = G::L1;
@@ -279,6 +279,21 @@ __global__ void __launch_bounds__(128) k_rows_inv(XiArgs<T> a) {
         double mm = block_max(mx, sm.red);
         finalize_partials(a.red, &mm);
     }
+}
+
+// one problem per launch
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_rows_fwd(XfArgs<T> a) { rows_fwd_body<T, M, MODE>(a); }
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_rows_inv(XiArgs<T> a) { rows_inv_body<T, M, MODE>(a); }
+// many problems of the same size per launch: blockIdx.y selects the problem's arguments
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_rows_fwd_b(const XfArgs<T>* __restrict__ args) {
+    rows_fwd_body<T, M, MODE>(args[blockIdx.y]);
+}
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_rows_inv_b(const XiArgs<T>* __restrict__ args) {
+    rows_inv_body<T, M, MODE>(args[blockIdx.y]);
 }
 
 template <typename T, int M, int MODE>
