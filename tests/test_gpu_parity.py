@@ -187,3 +187,34 @@ def test_subproblem_parity_mixed(lbtr, case):
     assert osp.model_value(p, phi_in, g_ref, d_in) >= f_ref - 1e-9 * abs(f_ref)
     assert abs(f_gpu - f_ref) <= 1e-5 * abs(f_ref)
     assert abs(info["model_value"] - f_gpu) <= 1e-5 * abs(f_ref)
+
+
+
+@pytest.fixture(scope="module")
+def scale256():
+    # the 256^3 scale workload; phi and v are float32-representable with zero mean so that
+    # one oracle evaluation serves both precisions
+    w = inputs.config_3d_scale(256)
+    phi = inputs.remove_mean(w.phi0.astype(np.float32).astype(np.float64))
+    v = inputs.gaussian_field(w.shape, 1.0, 104).astype(np.float32).astype(np.float64)
+    p = olb.Problem.from_workload(w)
+    return (w, phi, v, olb.hessvec(p, phi, v - v.mean()), olb.gradient(p, phi), olb.energy(p, phi))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hessvec_and_gradient_parity_256cubed(lbtr, scale256, prec):
+    # 3D grids above 128^3 take the register row kernels and the persistent line passes
+    w, phi, v, hv_ref, g_ref, e_ref = scale256
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    phi_t = torch.tensor(phi, dtype=dt, device=DEV)
+    v_t = torch.tensor(v, dtype=dt, device=DEV)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED)
+    hv = torch.empty_like(v_t)
+    lbtr.lb_hessvec(ctx, phi_t, v_t, hv)
+    g = torch.empty_like(phi_t)
+    e, _ = lbtr.lb_energy_grad(ctx, phi_t, g)
+    torch.cuda.synchronize()
+    fp64 = prec == "fp64"
+    assert _rel(hv.double().cpu().numpy(), hv_ref) < (1e-12 if fp64 else 2e-5)
+    assert _rel(g.double().cpu().numpy(), g_ref) < (1e-10 if fp64 else 2e-5)
+    assert abs(e - e_ref) <= (1e-12 if fp64 else 1e-6) * abs(e_ref)
