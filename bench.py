@@ -24,6 +24,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -76,7 +77,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.idx = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+        # the raw samples go to LB_CLOCKS_DIR (default: the system temporary directory)
+        self.path = os.path.join(os.environ.get("LB_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{gpu_index}.csv")
 
     def start(self):
         try:

@@ -284,8 +284,8 @@ lb_status lb_profile_read(lb_ctx *ctx, int kclass, double *total_ms, long long *
                           double *alg_bytes);
 
 /*
- * Batches of independent problems, for parameter sweeps (SURVEY-planned phase-diagram
- * sweep over (tau, gamma, M); the paper solves one problem at a time and has no batch
+ * Batches of independent problems, for parameter sweeps (phase-diagram sweeps over
+ * (tau, gamma, M); the paper solves one problem at a time and has no batch
  * interface).  A batch owns one context per problem; the problems may differ in grid
  * size, dimension, box and parameters, and share the precision.
  *   probs [in]  `count` problem descriptions (copied).
