@@ -18,4 +18,6 @@ Modules and what pins them (tests/test_oracle_*.py):
   trust_region Algorithms 1, 2    <- second-order stationarity at exit (dense
                                      eigenvalues), PCG vs dense solve
   eig          lambda_min         <- dense eigendecomposition, closed form at psi = 0
+  first_order  semi-implicit      <- closed-form step on a single cosine mode,
+               gradient flow         monotone energy decrease, fixed points = zeros of g
 """
