@@ -242,6 +242,42 @@ lb_status lb_imex_tr_solve(lb_ctx *ctx, double *phi_inout, const lb_tr_opts *opt
                            lb_tr_info *info, lb_stream stream);
 
 /*
+ * First-order gradient flow: the semi-implicit scheme (SIS) among the gradient-flow
+ * methods §4 compares with, and the source of the first-order trajectories that §4
+ * "Robustness to initial conditions" starts IMEX-TR from (initial, intermediate and
+ * converged states).  The paper does not print the scheme; each step here treats the
+ * reciprocal diagonal D = Lambda implicitly and F'(phi) explicitly, as the IMEX
+ * subproblem solver of §3.2 does:
+ *     phi <- phi - dt (I + dt D)^{-1} g(phi),
+ * with the k = 0 coefficient held at zero, so that its fixed points are the zeros of g.
+ * Computed in FP64 in both precisions.
+ *   phi_inout [in/out] DEVICE array of N doubles, zero mean, 16-byte aligned.
+ *   opts      NULL for the defaults (dt 1, eps 1e-8, max_steps 10000, check_every 10).
+ *   info      [out] may be NULL.
+ * max_x |g| is tested before the first step, every check_every steps and after the last
+ * one; the solve stops when it is below eps.  Returns LB_ERR_NOCONV after max_steps steps
+ * without that (phi_inout holds the last iterate), LB_ERR_INVALID_ARG for dt <= 0 or
+ * max_steps < 0, LB_ERR_NOT_ZERO_MEAN / LB_ERR_NONFINITE as lb_energy_grad.
+ */
+typedef struct {
+    double dt;           /* time step */
+    double eps;          /* stop when max_x |g(x)| < eps */
+    int max_steps;       /* cap on steps */
+    int check_every;     /* steps between tests of max |g| (each test synchronises) */
+} lb_sis_opts;
+
+typedef struct {
+    int steps;           /* steps taken */
+    double energy;       /* E at the last test */
+    double gmax;         /* max_x |g| at the last test */
+    int status;          /* lb_status of the solve */
+} lb_sis_info;
+
+void lb_default_sis_opts(lb_sis_opts *o);
+lb_status lb_sis_solve(lb_ctx *ctx, double *phi_inout, const lb_sis_opts *opts, lb_sis_info *info,
+                       lb_stream stream);
+
+/*
  * Hessian-vector product that allocates nothing (no counterpart in the paper; an
  * interface for callers that cannot call cudaMalloc, e.g. plug-ins whose host
  * framework owns all device memory, or loops that cannot afford the implicit device

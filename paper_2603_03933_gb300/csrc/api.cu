@@ -238,4 +238,29 @@ lb_status lb_imex_tr_solve(lb_ctx* ctx, double* phi_inout, const lb_tr_opts* opt
     return st;
 }
 
+void lb_default_sis_opts(lb_sis_opts* o) {
+    if (!o) return;
+    o->dt = 1.0;
+    o->eps = 1e-8;
+    o->max_steps = 10000;
+    o->check_every = 10;
+}
+
+lb_status lb_sis_solve(lb_ctx* ctx, double* phi_inout, const lb_sis_opts* opts, lb_sis_info* info,
+                       lb_stream stream) {
+    if (!ctx || !phi_inout) return fail(ctx, LB_ERR_INVALID_ARG, "lb_sis_solve: null argument");
+    if (!aligned16(phi_inout)) return fail(ctx, LB_ERR_INVALID_ARG, "lb_sis_solve: field must be 16-byte aligned");
+    lb_sis_opts o;
+    lb_default_sis_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.dt > 0.0) || !std::isfinite(o.dt) || o.max_steps < 0)
+        return fail(ctx, LB_ERR_INVALID_ARG, "lb_sis_solve: dt must be positive and max_steps >= 0");
+    lb_sis_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    lb_status st = ctx->sis_solve(phi_inout, o, &inf, (cudaStream_t)stream);
+    inf.status = (int)st;
+    if (info) *info = inf;
+    return st;
+}
+
 }  // extern "C"

@@ -217,4 +217,5 @@ struct lb_ctx {
                                                 unsigned stream, cudaStream_t s);
 
     lb_status tr_solve(double* phi, const lb_tr_opts& o, lb_tr_info* info, cudaStream_t s);
+    lb_status sis_solve(double* phi, const lb_sis_opts& o, lb_sis_info* info, cudaStream_t s);
 };

@@ -444,3 +444,37 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
     }
     return result;
 }
+
+// ---------------------------------------------------------------------------------
+// Semi-implicit gradient flow: phi <- phi - dt (I + dt Lambda)^{-1} g(phi), i.e. the
+// preconditioner of the CONTRACT solves at shift 1/dt applied to g and subtracted
+// (dt (I + dt Lambda)^{-1} = (Lambda + 1/dt)^{-1}); FP64.
+// ---------------------------------------------------------------------------------
+lb_status lb_ctx::sis_solve(double* phi, const lb_sis_opts& o, lb_sis_info* info, cudaStream_t s) {
+    Plan<double>& p = *p64;
+    double* g = f64[0];
+    double* z = f64[1];
+    lb_status st;
+    double e = 0.0, gm = 0.0;
+    info->steps = 0;
+    if ((st = energy_grad(p, (const double*)phi, &e, g, &gm, s))) return st;
+    const int ce = std::max(1, o.check_every);
+    int steps = 0;
+    while (!(gm < o.eps) && steps < o.max_steps) {
+        p.precond(g, z, 1.0 / o.dt, s);
+        p.axpby(phi, z, -1.0, 1.0, s);
+        ++steps;
+        if (steps % ce == 0 || steps == o.max_steps) {
+            if ((st = energy_grad(p, (const double*)phi, &e, g, &gm, s))) break;
+        } else {
+            p.energy_grad(phi, g, s);
+            if ((st = launch_status("lb_sis_solve"))) break;
+        }
+    }
+    info->steps = steps;
+    info->energy = e;
+    info->gmax = gm;
+    if (st) return st;
+    if (!(gm < o.eps)) { err = "lb_sis_solve: step cap reached"; return LB_ERR_NOCONV; }
+    return LB_OK;
+}

@@ -72,6 +72,16 @@ class lb_tr_info(ctypes.Structure):
                 ("randomized", ctypes.c_int), ("g1_min", ctypes.c_double)]
 
 
+class lb_sis_opts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("eps", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("check_every", ctypes.c_int)]
+
+
+class lb_sis_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("energy", ctypes.c_double), ("gmax", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
 # (name, restype, argtypes) of every exported entry point declared in include/lbtr.h
 _VP, _D, _DP = ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
 SIGNATURES = [
@@ -91,6 +101,8 @@ SIGNATURES = [
                                      ctypes.POINTER(lb_eig_info), _VP]),
     ("lb_default_tr_opts", None, [ctypes.POINTER(lb_tr_opts)]),
     ("lb_imex_tr_solve", ctypes.c_int, [_VP, _VP, ctypes.POINTER(lb_tr_opts), ctypes.POINTER(lb_tr_info), _VP]),
+    ("lb_default_sis_opts", None, [ctypes.POINTER(lb_sis_opts)]),
+    ("lb_sis_solve", ctypes.c_int, [_VP, _VP, ctypes.POINTER(lb_sis_opts), ctypes.POINTER(lb_sis_info), _VP]),
     ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
@@ -310,6 +322,25 @@ def lb_imex_tr_solve(ctx: Context, phi64, opts: lb_tr_opts | None = None, stream
             "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
             "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": st,
             "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None}
+
+
+def default_sis_opts() -> lb_sis_opts:
+    o = lb_sis_opts()
+    load().lb_default_sis_opts(ctypes.byref(o))
+    return o
+
+
+def lb_sis_solve(ctx: Context, phi64, opts: lb_sis_opts | None = None, stream=None,
+                 raise_on_noconv: bool = True) -> dict:
+    """Semi-implicit gradient flow (C: lb_sis_solve); phi64 (float64 CUDA tensor) is updated in place."""
+    torch = _torch()
+    o = opts if opts is not None else default_sis_opts()
+    info = lb_sis_info()
+    st = load().lb_sis_solve(ctx.handle, _ptr(ctx, phi64, "phi", torch.float64), ctypes.byref(o),
+                             ctypes.byref(info), _stream(stream))
+    if not (st == 4 and not raise_on_noconv):
+        _check(ctx, st, "lb_sis_solve")
+    return {"steps": info.steps, "energy": info.energy, "gmax": info.gmax, "status": st}
 
 
 def lb_set_barrier_budget(ctx: Context, cycles: int):
