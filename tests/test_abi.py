@@ -46,6 +46,12 @@ def test_default_options_match_the_paper(lib):
     assert (o.sub.eta, o.sub.eps_sub) == (0.1, 1e-13)
 
 
+def test_default_first_order_options(lib):
+    from paper_2603_03933_gb300 import lbtr
+    o = lbtr.default_sis_opts()
+    assert (o.dt, o.eps, o.max_steps, o.check_every) == (1.0, 1e-8, 10000, 10)
+
+
 def test_create_rejects_bad_sizes_without_a_gpu(lib):
     # argument validation happens before any CUDA call
     from paper_2603_03933_gb300 import lbtr
