@@ -339,6 +339,31 @@ def time_sweep(lbtr, rank: int, world: int, n_instances: int, replays: int = 20)
             "gpu_launches": 3 * len(sizes) * replays}
 
 
+def time_sweep_solve(lbtr, rank: int, world: int, n_instances: int, threads: int = 16) -> dict:
+    """Whole IMEX-TR solves of a sweep (2D instances of the batched sweep's recipe, M in
+    {64, 128}, mixed, eps 1e-8) through lb_batch_tr_solve on `threads` host threads; wall
+    clock of the one call, instances sharded across ranks, max over ranks."""
+    import torch
+    from paper_2603_03933_gb300 import inputs
+    ws = [inputs.batched_sweep(n_instances, seed=5, sizes=(64, 128))[i] for i in shard(n_instances, rank, world)]
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, lbtr.LB_MIXED)
+    o = lbtr.default_tr_opts()
+    o.eps, o.max_outer = 1e-8, 300
+    phis = [torch.tensor(w.phi0, dtype=torch.float64, device="cuda") for w in ws]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    infos = lbtr.lb_batch_tr_solve(batch, phis, opts=o, nthreads=threads, raise_on_error=False)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    return {"workload": f"{n_instances} 2D instances, M in {{64,128}} (seed 5), mixed, IMEX-TR to "
+                        f"max|g| < 1e-8 with the second-order test; {threads} host threads, one call",
+            "value": whole_job_rate(len(ws), dt, world), "unit": "instances/s", "seconds": dt,
+            "instances_per_rank": len(ws), "converged": sum(1 for i in infos if i["status"] == 0),
+            "outer_iters": sum(i["outer"] for i in infos), "inner_iters": sum(i["inner"] for i in infos)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +379,8 @@ def main():
     ap.add_argument("--tr-outer", type=int, default=4, help="outer IMEX-TR iterations timed per precision")
     ap.add_argument("--sweep-instances", type=int, default=256,
                     help="instances of the batched 2D sweep timed as one CUDA graph (0: skip)")
+    ap.add_argument("--sweep-solve-instances", type=int, default=16,
+                    help="instances of the sweep solved whole by lb_batch_tr_solve (0: skip)")
     ap.add_argument("--profile-sub", type=int, default=0,
                     help="profile this many IMEX inner iterations per precision and exit")
     args = ap.parse_args()
@@ -520,6 +547,12 @@ def main():
     # x rows, y lines, z lines (with Lambda), y lines, inverse x rows
     launches_per_hvp = 3 if 32 <= M <= 128 else 5
     sweep = time_sweep(lbtr, rank, world, args.sweep_instances) if args.sweep_instances > 0 else None
+    sweep_solve = None
+    if args.sweep_solve_instances > 0:
+        try:
+            sweep_solve = time_sweep_solve(lbtr, rank, world, args.sweep_solve_instances)
+        except Exception as ex:  # report, do not hide
+            sweep_solve = {"error": str(ex)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
@@ -530,7 +563,7 @@ def main():
                    "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_hvp * args.batch * args.steps,
-        "fp64": fp64, "size_256": big, "tr": tr, "sweep": sweep,
+        "fp64": fp64, "size_256": big, "tr": tr, "sweep": sweep, "sweep_solve": sweep_solve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -348,6 +348,25 @@ int lb_batch_size(const lb_batch *batch);
 lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *const *v, void *const *hv,
                            lb_stream stream);
 
+/*
+ * Algorithm 1 (as lb_imex_tr_solve) for every problem of the batch, several at a time: a
+ * pool of host threads, each with its own internal stream, takes the problems from a
+ * shared queue, largest first, so that the GPU works on several problems while each
+ * driver waits for its scalars.  The solves start after the work already queued on
+ * `stream` and the call returns when all have ended (later work on `stream` is ordered
+ * after them).
+ *   phi      [in/out] host array of lb_batch_size() DEVICE pointers, each N doubles as in
+ *            lb_imex_tr_solve, distinct and 16-byte aligned.
+ *   opts     options shared by all problems (NULL: the defaults).
+ *   info     [out] host array of lb_batch_size() results, or NULL.
+ *   nthreads host threads (<= 0: 8); at most the batch size and 16.
+ * Returns LB_OK if every solve returned LB_OK, else the status of the first problem (in
+ * batch order) that did not, whose message lb_batch_last_error then holds; every problem
+ * is solved either way and info[i].status holds each one's status.
+ */
+lb_status lb_batch_tr_solve(lb_batch *batch, double *const *phi, const lb_tr_opts *opts, lb_tr_info *info,
+                            int nthreads, lb_stream stream);
+
 /* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
  * (0 restores the default of about two seconds).  Lets tests exercise the
  * LB_ERR_TIMEOUT path without a hang. */

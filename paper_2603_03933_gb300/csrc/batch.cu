@@ -10,9 +10,16 @@
 // (a longest-first list schedule); they share no data and no scratch (one context each),
 // so the GPU runs them side by side.  The graph is recorded on the first call with a given
 // set of field pointers and replayed by later calls with the same pointers.
+//
+// Whole solves of a batch (lb_batch_tr_solve) run on a pool of host threads, one side
+// stream each, that take problems from a shared queue, largest first; each thread drives
+// Algorithm 1 for its problem as lb_imex_tr_solve does, so the GPU works on several
+// problems at once while each driver waits on its own scalars.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ctx.cuh"
@@ -263,6 +270,54 @@ lb_status lb_batch_hessvec(lb_batch* b, const void* const* phi, const void* cons
         b->key = key;
     }
     return batch_cuda(b, cudaGraphLaunch(b->exec, (cudaStream_t)stream), "lb_batch_hessvec/launch");
+}
+
+lb_status lb_batch_tr_solve(lb_batch* b, double* const* phi, const lb_tr_opts* opts, lb_tr_info* info,
+                            int nthreads, lb_stream stream) {
+    if (!b || !phi) return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_tr_solve: null argument");
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i) {
+        if (!phi[i]) return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_tr_solve: null field pointer");
+        if ((uintptr_t)phi[i] & 15u)
+            return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_tr_solve: fields must be 16-byte aligned");
+        for (int j = 0; j < i; ++j)
+            if (phi[j] == phi[i]) return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_tr_solve: aliased fields");
+    }
+    const int nw = std::max(1, std::min({nthreads > 0 ? nthreads : 8, n, b->nstreams}));
+    int dev = 0;
+    lb_status st = batch_cuda(b, cudaGetDevice(&dev), "lb_batch_tr_solve");
+    // the solves start after the caller's stream has produced the fields
+    if (!st) st = batch_cuda(b, cudaEventRecord(b->fork, (cudaStream_t)stream), "lb_batch_tr_solve");
+    for (int k = 0; k < nw && !st; ++k)
+        st = batch_cuda(b, cudaStreamWaitEvent(b->side[k], b->fork, 0), "lb_batch_tr_solve");
+    if (st) return st;
+    std::vector<lb_tr_info> inf(n);
+    std::vector<int> status(n, (int)LB_ERR_CUDA);     // until a worker has solved the problem
+    std::atomic<int> next(0);
+    auto worker = [&](int k) {
+        if (cudaSetDevice(dev) != cudaSuccess) return;     // the other workers take its share
+        for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+            const int i = b->order[q];
+            status[i] = (int)lb_imex_tr_solve(b->ctx[i], phi[i], opts, &inf[i], (lb_stream)b->side[k]);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int k = 1; k < nw; ++k) pool.emplace_back(worker, k);
+    worker(0);
+    for (std::thread& t : pool) t.join();
+    // later work on the caller's stream sees the solved fields
+    for (int k = 0; k < nw && !st; ++k) {
+        st = batch_cuda(b, cudaEventRecord(b->join[k], b->side[k]), "lb_batch_tr_solve");
+        if (!st) st = batch_cuda(b, cudaStreamWaitEvent((cudaStream_t)stream, b->join[k], 0), "lb_batch_tr_solve");
+    }
+    if (info) for (int i = 0; i < n; ++i) info[i] = inf[i];
+    for (int i = 0; i < n && !st; ++i)
+        if (status[i] != LB_OK) {
+            st = (lb_status)status[i];
+            b->err = "lb_batch_tr_solve: problem " + std::to_string(i) + ": " +
+                     (next.load() > n ? lb_last_error(b->ctx[i]) : "no worker could select the device");
+        }
+    return st;
 }
 
 }  // extern "C"

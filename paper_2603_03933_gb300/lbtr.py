@@ -112,6 +112,8 @@ SIGNATURES = [
     ("lb_batch_last_error", ctypes.c_char_p, [_VP]),
     ("lb_batch_size", ctypes.c_int, [_VP]),
     ("lb_batch_hessvec", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("lb_batch_tr_solve", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(lb_tr_opts),
+                                         ctypes.POINTER(lb_tr_info), ctypes.c_int, _VP]),
 ]
 KERNEL_CLASSES = ["xfwd", "xinv", "xmid", "col_y", "col_inner", "secular", "reduce"]
 
@@ -441,3 +443,34 @@ def lb_batch_hessvec(batch: Batch, phis, vs, hvs, stream=None):
         msg = load().lb_batch_last_error(batch.handle)
         raise LBError(st, "lb_batch_hessvec: " + (msg.decode() if msg else ""))
     return hvs
+
+
+def _tr_info_dict(info: lb_tr_info) -> dict:
+    return {"outer": info.outer, "inner": info.inner, "accepted": info.accepted, "contracted": info.contracted,
+            "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
+            "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": info.status,
+            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None}
+
+
+def lb_batch_tr_solve(batch: Batch, phis, opts: lb_tr_opts | None = None, nthreads: int = 0, stream=None,
+                      raise_on_error: bool = True) -> list:
+    """IMEX-TR for every problem on a pool of host threads (C: lb_batch_tr_solve); each
+    phis[i] (float64 CUDA tensor) is updated in place.  Returns one info dict per problem."""
+    torch = _torch()
+    n = len(batch)
+    if len(phis) != n:
+        raise ValueError("one phi per problem")
+    arr = (_VP * n)()
+    for i, t in enumerate(phis):
+        dim, m = batch.meta[i]
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != m ** dim:
+            raise ValueError(f"field {i}: need a contiguous float64 CUDA tensor of {m ** dim} values")
+        arr[i] = t.data_ptr()
+    o = opts if opts is not None else default_tr_opts()
+    infos = (lb_tr_info * n)()
+    st = load().lb_batch_tr_solve(batch.handle, arr, ctypes.byref(o), infos, int(nthreads), _stream(stream))
+    if st != 0 and raise_on_error:
+        msg = load().lb_batch_last_error(batch.handle)
+        raise LBError(st, "lb_batch_tr_solve: " + (msg.decode() if msg else ""))
+    return [_tr_info_dict(infos[i]) for i in range(n)]
+

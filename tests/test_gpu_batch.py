@@ -79,3 +79,34 @@ def test_batch_rejects_bad_fields(lbtr):
     with pytest.raises(lbtr.LBError) as e:
         lbtr.lb_batch_hessvec(batch, f, f, f)          # outputs alias inputs
     assert e.value.status == 1
+
+
+def test_batch_tr_solve_matches_individual_solves(lbtr):
+    # eight 2D problems of two sizes across (tau, gamma), solved on four host threads; each
+    # must end where the single-problem driver ends (same stop test, same SP-II check)
+    ws = [w for w in inputs.batched_sweep(8, seed=11, sizes=(16, 32))]
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    o.eps, o.max_outer = 1e-8, 300
+    phis = [torch.tensor(w.phi0, dtype=torch.float64, device=DEV) for w in ws]
+    infos = lbtr.lb_batch_tr_solve(batch, phis, opts=o, nthreads=4)
+    for w, ph, info in zip(ws, phis, infos):
+        ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma, lbtr.LB_FP64)
+        ref = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+        r = lbtr.lb_imex_tr_solve(ctx, ref, opts=o)
+        assert info["status"] == 0 and info["gmax"] < 1e-8
+        assert abs(info["energy"] - r["energy"]) <= 1e-9 * max(1.0, abs(r["energy"]))
+        p = olb.Problem.from_workload(w)
+        x = ph.cpu().numpy()
+        assert np.max(np.abs(olb.gradient(p, x))) < 1e-8
+        assert abs(olb.energy(p, x) - info["energy"]) <= 1e-12
+
+
+def test_batch_tr_solve_rejects_aliased_fields(lbtr):
+    ws = inputs.batched_sweep(2, seed=12, sizes=(16,))
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, lbtr.LB_FP64)
+    ph = torch.tensor(ws[0].phi0, dtype=torch.float64, device=DEV)
+    with pytest.raises(lbtr.LBError):
+        lbtr.lb_batch_tr_solve(batch, [ph, ph])
