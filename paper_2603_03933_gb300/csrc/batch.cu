@@ -302,7 +302,13 @@ lb_status lb_batch_tr_solve(lb_batch* b, double* const* phi, const lb_tr_opts* o
         }
     };
     std::vector<std::thread> pool;
-    for (int k = 1; k < nw; ++k) pool.emplace_back(worker, k);
+    for (int k = 1; k < nw; ++k) {
+        try {
+            pool.emplace_back(worker, k);
+        } catch (...) {     // no exception crosses the C ABI: run with the threads already started
+            break;
+        }
+    }
     worker(0);
     for (std::thread& t : pool) t.join();
     // later work on the caller's stream sees the solved fields
