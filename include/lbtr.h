@@ -362,7 +362,9 @@ lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *
  *   nthreads host threads (<= 0: 8); at most the batch size and 16.
  * Returns LB_OK if every solve returned LB_OK, else the status of the first problem (in
  * batch order) that did not, whose message lb_batch_last_error then holds; every problem
- * is solved either way and info[i].status holds each one's status.
+ * is solved either way and info[i].status holds each one's status.  Blocks the calling
+ * thread; other calls on the same batch must not run meanwhile (they share its streams
+ * and contexts).
  */
 lb_status lb_batch_tr_solve(lb_batch *batch, double *const *phi, const lb_tr_opts *opts, lb_tr_info *info,
                             int nthreads, lb_stream stream);
