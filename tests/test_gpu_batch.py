@@ -53,10 +53,10 @@ def test_batch_matches_single_problem_products(lbtr, prec):
         lbtr.lb_hessvec(c, phi, v, hv)
         refs.append(hv)
     torch.cuda.synchronize()
-    for rnd in range(3):
-        # rounds 0 and 1 share pointers (record, replay); round 2 uses new outputs (record anew)
-        hvs = [torch.full_like(v, float("nan")) for v in vs] if rnd != 1 else hvs
-        if rnd == 1:
+    for call in range(3):
+        # calls 0 and 1 share pointers (record, replay); call 2 uses new outputs (record anew)
+        hvs = [torch.full_like(v, float("nan")) for v in vs] if call != 1 else hvs
+        if call == 1:
             for h in hvs:
                 h.fill_(float("nan"))
         lbtr.lb_batch_hessvec(batch, phis, vs, hvs)
