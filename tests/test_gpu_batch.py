@@ -62,7 +62,7 @@ def test_batch_matches_single_problem_products(lbtr, prec):
         lbtr.lb_batch_hessvec(batch, phis, vs, hvs)
         torch.cuda.synchronize()
         for i, (h, r) in enumerate(zip(hvs, refs)):
-            assert _rel(h.double().cpu().numpy(), r.double().cpu().numpy()) <= tol, (rnd, i)
+            assert _rel(h.double().cpu().numpy(), r.double().cpu().numpy()) <= tol, (call, i)
     # two members against the oracle (parity tolerances)
     for i in (0, len(ws) - 2):
         w = ws[i]
