@@ -62,3 +62,14 @@ def test_create_rejects_bad_sizes_without_a_gpu(lib):
     with pytest.raises(lbtr.LBError) as e:
         lbtr.lb_create(2, 64, (0.0, 1.0), 1.0, -0.1, 0.2)
     assert e.value.status == 1
+
+
+def test_batch_solve_binding_checks_fields_before_the_call():
+    # host-side marshalling errors are raised before anything reaches the library
+    torch = pytest.importorskip("torch")
+    from paper_2603_03933_gb300 import lbtr
+    b = lbtr.Batch(None, [(2, 16), (2, 16)], lbtr.LB_FP64)
+    with pytest.raises(ValueError):
+        lbtr.lb_batch_tr_solve(b, [torch.zeros(256, dtype=torch.float64)])
+    with pytest.raises(ValueError):      # host tensors are not device fields
+        lbtr.lb_batch_tr_solve(b, [torch.zeros(256, dtype=torch.float64)] * 2)
