@@ -215,6 +215,17 @@ typedef struct {
      * |<g, u>_N| <= hard_tol (the component g^(1) of g along u), the subproblem starts
      * from a random point of the trust region instead of -r g / ||g||.  0: off. */
     double hard_tol;
+    /* Checkpoint / resume (no counterpart in the paper).  If checkpoint_path is non-NULL
+     * and checkpoint_every > 0, the state carried between outer iterations (the iterate
+     * and the scalars of Algorithm 1) is written to <checkpoint_path>.npy and .json after
+     * every checkpoint_every-th outer iteration.  If resume != 0, the solve starts from
+     * that checkpoint instead of phi_inout and repeats the remaining iterations exactly;
+     * max_outer still counts from the first iteration of the original solve.  The path
+     * is borrowed for the duration of the call.  Errors: LB_ERR_INVALID_ARG when a file
+     * cannot be written or read, or holds another grid. */
+    const char *checkpoint_path;
+    int checkpoint_every;
+    int resume;
 } lb_tr_opts;
 
 typedef struct {
@@ -357,7 +368,8 @@ lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *
  * after them).
  *   phi      [in/out] host array of lb_batch_size() DEVICE pointers, each N doubles as in
  *            lb_imex_tr_solve, distinct and 16-byte aligned.
- *   opts     options shared by all problems (NULL: the defaults).
+ *   opts     options shared by all problems (NULL: the defaults); problem i checkpoints
+ *            to (and resumes from) <checkpoint_path>.<i>.
  *   info     [out] host array of lb_batch_size() results, or NULL.
  *   nthreads host threads (<= 0: 8); at most the batch size and 16.
  * Returns LB_OK if every solve returned LB_OK, else the status of the first problem (in

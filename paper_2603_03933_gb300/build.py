@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbtr.so")
-SOURCES = ["plan_f64.cu", "plan_f32.cu", "api.cu", "solver.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["plan_f64.cu", "plan_f32.cu", "api.cu", "solver.cu", "noalloc.cu", "batch.cu", "checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -70,6 +70,9 @@ void lb_default_tr_opts(lb_tr_opts* o) {
     o->pcg_max_iter = 2000;
     o->pcg_rtol = 1e-10;
     o->hard_tol = 0.0;
+    o->checkpoint_path = nullptr;
+    o->checkpoint_every = 0;
+    o->resume = 0;
 }
 
 lb_status lb_create(const lb_problem* prob, lb_precision prec, lb_ctx** out) {

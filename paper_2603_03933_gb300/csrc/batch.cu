@@ -298,7 +298,15 @@ lb_status lb_batch_tr_solve(lb_batch* b, double* const* phi, const lb_tr_opts* o
         if (cudaSetDevice(dev) != cudaSuccess) return;     // the other workers take its share
         for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
             const int i = b->order[q];
-            status[i] = (int)lb_imex_tr_solve(b->ctx[i], phi[i], opts, &inf[i], (lb_stream)b->side[k]);
+            lb_tr_opts oi;
+            lb_default_tr_opts(&oi);
+            if (opts) oi = *opts;
+            std::string cp;     // each problem checkpoints to its own files
+            if (oi.checkpoint_path) {
+                cp = std::string(oi.checkpoint_path) + "." + std::to_string(i);
+                oi.checkpoint_path = cp.c_str();
+            }
+            status[i] = (int)lb_imex_tr_solve(b->ctx[i], phi[i], &oi, &inf[i], (lb_stream)b->side[k]);
         }
     };
     std::vector<std::thread> pool;

@@ -7,6 +7,7 @@
 #include <limits>
 #include <vector>
 
+#include "checkpoint.h"
 #include "ctx.cuh"
 #include "dense_eig.cuh"
 
@@ -284,9 +285,51 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
     const char* tr_env = std::getenv("LBTR_TRACE");
     const bool trace = tr_env && tr_env[0] == '1';   // one JSON line per outer iteration on stderr
     lb_status result = LB_ERR_NOCONV;
-    int j = 0;
+    int j = 0, j0 = 0;
     double E = 0.0, gmax = 0.0;
-    for (j = 0; j < o.max_outer; ++j) {
+    if (o.resume && o.checkpoint_path) {
+        TrCheckpoint c;
+        std::vector<double> field;
+        std::string e;
+        if (!read_checkpoint(o.checkpoint_path, c, field, e)) { err = "lb_imex_tr_solve: " + e; return LB_ERR_INVALID_ARG; }
+        if (c.dim != prob.dim || c.n != prob.n || (long long)field.size() != P.n()) {
+            err = "lb_imex_tr_solve: the checkpoint holds another grid";
+            return LB_ERR_INVALID_ARG;
+        }
+        cudaMemcpyAsync(v, field.data(), field.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+        cudaError_t ce = cudaStreamSynchronize(s);      // the host copy goes out of scope below
+        if (ce != cudaSuccess) { err = std::string("lb_imex_tr_solve: ") + cudaGetErrorString(ce); return LB_ERR_CUDA; }
+        S = TrState{c.r, c.nu, c.mu, c.rho_prev, c.have_rho != 0};
+        random_next = c.random_next != 0;
+        rstream = c.rstream;
+        j0 = c.j;
+        info->accepted = c.accepted;
+        info->contracted = c.contracted;
+        info->shrunk = c.shrunk;
+        info->randomized = c.randomized;
+        info->inner = c.inner;
+        info->g1_min = c.g1_min;
+    }
+    // the state carried into outer iteration `next`, written to the checkpoint files
+    auto checkpoint = [&](int next) -> lb_status {
+        std::vector<double> field((size_t)P.n());
+        cudaMemcpyAsync(field.data(), v, field.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { err = std::string("lb_imex_tr_solve: ") + cudaGetErrorString(ce); return LB_ERR_CUDA; }
+        TrCheckpoint c;
+        c.dim = prob.dim; c.n = prob.n; c.j = next;
+        c.r = S.r; c.nu = S.nu; c.mu = S.mu; c.rho_prev = S.rho_prev; c.have_rho = S.have_rho ? 1 : 0;
+        c.random_next = random_next ? 1 : 0; c.rstream = rstream;
+        c.accepted = info->accepted; c.contracted = info->contracted; c.shrunk = info->shrunk;
+        c.randomized = info->randomized; c.inner = info->inner; c.g1_min = info->g1_min;
+        std::string e;
+        if (!write_checkpoint(o.checkpoint_path, c, field.data(), (long long)field.size(), e)) {
+            err = "lb_imex_tr_solve: " + e;
+            return LB_ERR_INVALID_ARG;
+        }
+        return LB_OK;
+    };
+    for (j = j0; j < o.max_outer; ++j) {
         if ((st = energy_grad<double>(P, v, &E, g, &gmax, s))) return st;
         info->energy = E;
         info->gmax = gmax;
@@ -433,6 +476,8 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
                          "\"acc\": %d, \"con\": %d, \"shr\": %d}\n",
                          j, E, gmax, S.r, S.nu, S.mu, lam, sn, rho, si.iterations, (int)ss, info->accepted,
                          info->contracted, info->shrunk);
+        if (o.checkpoint_path && o.checkpoint_every > 0 && (j + 1) % o.checkpoint_every == 0)
+            if ((st = checkpoint(j + 1))) return st;
     }
     info->outer = j;
     if (result != LB_OK) {

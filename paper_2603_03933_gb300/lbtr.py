@@ -62,7 +62,8 @@ class lb_tr_opts(ctypes.Structure):
                 ("mu0", ctypes.c_double), ("r0", ctypes.c_double), ("nu0", ctypes.c_double),
                 ("eps", ctypes.c_double), ("max_outer", ctypes.c_int), ("second_order", ctypes.c_int),
                 ("tol2", ctypes.c_double), ("sub", lb_sub_opts), ("eig", lb_eig_opts),
-                ("pcg_max_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("hard_tol", ctypes.c_double)]
+                ("pcg_max_iter", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("hard_tol", ctypes.c_double),
+                ("checkpoint_path", ctypes.c_char_p), ("checkpoint_every", ctypes.c_int), ("resume", ctypes.c_int)]
 
 
 class lb_tr_info(ctypes.Structure):

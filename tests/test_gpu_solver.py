@@ -177,3 +177,46 @@ def test_tr_solve_3d_bcc_mixed_matches_fp64(lbtr):
         out[prec] = info
     assert abs(out["mixed"]["energy"] - out["fp64"]["energy"]) < 1e-8
     assert (out["mixed"]["lambda_min"] >= -1e-8) == (out["fp64"]["lambda_min"] >= -1e-8)
+
+
+def test_tr_checkpoint_resume_repeats_the_solve(lbtr, tmp_path):
+    # a solve cut after four outer iterations (checkpoints after the 2nd and 4th) and resumed
+    # from its files ends where the uninterrupted solve ends, iteration for iteration
+    w = inputs.random_problem((16, 16), 5, sigma=0.05, tau=-0.2, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    o.eps, o.max_outer = 1e-8, 200
+    straight = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    ref = lbtr.lb_imex_tr_solve(ctx, straight, opts=o)
+    assert ref["outer"] > 4
+    path = str(tmp_path / "tr").encode()
+    o.checkpoint_path, o.checkpoint_every, o.max_outer = path, 2, 4
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    cut = lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    assert cut["status"] == 4 and cut["outer"] == 4
+    saved = np.load(path.decode() + ".npy")
+    assert np.array_equal(saved, phi.cpu().numpy())
+    o.resume, o.max_outer = 1, 200
+    resumed = torch.zeros_like(phi)                      # the start comes from the files
+    info = lbtr.lb_imex_tr_solve(ctx, resumed, opts=o)
+    assert info["outer"] == ref["outer"] and info["inner"] == ref["inner"]
+    assert (info["accepted"], info["contracted"], info["shrunk"]) == (ref["accepted"], ref["contracted"], ref["shrunk"])
+    assert np.max(np.abs(resumed.cpu().numpy() - straight.cpu().numpy())) <= 1e-13
+    assert abs(info["energy"] - ref["energy"]) <= 1e-14
+
+
+def test_tr_resume_refuses_a_checkpoint_of_another_grid(lbtr, tmp_path):
+    w = inputs.random_problem((16, 16), 6, sigma=0.05, tau=-0.2, gamma=0.3)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    path = str(tmp_path / "other")
+    np.save(path + ".npy", np.zeros((32, 32)))
+    with open(path + ".json", "w") as f:
+        f.write('{"format": 1, "dim": 2, "n": 32, "j": 1, "r": 1, "nu": 5, "mu": 1, "rho_prev": 0, '
+                '"have_rho": 0, "random_next": 0, "rstream": 1, "accepted": 0, "contracted": 0, "shrunk": 0, '
+                '"randomized": 0, "inner": 0, "g1_min": NaN}\n')
+    o = lbtr.default_tr_opts()
+    o.checkpoint_path, o.resume = path.encode(), 1
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    with pytest.raises(lbtr.LBError) as e:
+        lbtr.lb_imex_tr_solve(ctx, phi, opts=o)
+    assert e.value.status == 1
