@@ -248,6 +248,9 @@ void lb_default_tr_opts(lb_tr_opts *o);
  * precisions (the outer iterate, gradient and ratio test are kept in FP64); in
  * LB_MIXED the inner iterations run in float.
  * Returns LB_ERR_NOCONV if max_outer is reached (phi_inout holds the last iterate).
+ * With the environment variable LBTR_TRACE=1, every outer iteration prints one JSON line
+ * on stderr: j, E, max|g|, r, nu, mu, lambda, ||s||, rho, inner iterations, the
+ * subproblem's status and the accepted / contracted / shrunk counts.
  */
 lb_status lb_imex_tr_solve(lb_ctx *ctx, double *phi_inout, const lb_tr_opts *opts,
                            lb_tr_info *info, lb_stream stream);
