@@ -168,24 +168,66 @@ def shard(n_items: int, rank: int, world: int) -> list:
     return list(range(rank, n_items, world))
 
 
-def oracle_hvp_rate(M: int, seconds: float = 12.0) -> dict:
-    """The FP64 CPU oracle's Hessian-vector products on the same workload (bounded sample)."""
-    import numpy as np
-    from oracle import lb as olb
-    from paper_2603_03933_gb300 import inputs
-    w = inputs.config_3d_scale(M)
-    p = olb.Problem.from_workload(w)
-    rng = np.random.default_rng(77)
-    done, t0 = 0, time.perf_counter()
-    while True:
-        v = inputs.remove_mean(rng.standard_normal(w.shape))
-        olb.hessvec(p, w.phi0, v)
-        done += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or done >= 50:
-            break
-    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} FP64 oracle Hessian-vector products at {M}^3 ({el:.1f} s, numpy, 1 thread)"}
+def _oracle_worker(M: int, seconds: float, seed: int, barrier, queue):
+    """One host core: FP64 oracle Hessian-vector products for `seconds` after all workers
+    are ready; puts (products, elapsed seconds), or an error text, on the queue."""
+    try:
+        import numpy as np
+        from oracle import lb as olb
+        from paper_2603_03933_gb300 import inputs
+        w = inputs.config_3d_scale(M)
+        p = olb.Problem.from_workload(w)
+        v = inputs.remove_mean(np.random.default_rng(seed).standard_normal(w.shape))
+        barrier.wait(timeout=300)
+        done, t0 = 0, time.perf_counter()
+        while True:
+            olb.hessvec(p, w.phi0, v)
+            done += 1
+            el = time.perf_counter() - t0
+            if el >= seconds or done >= 50:
+                break
+        queue.put((done, el))
+    except Exception as ex:  # reported by the parent
+        queue.put(f"{type(ex).__name__}: {ex}")
+
+
+def oracle_hvp_rate(M: int, seconds: float = 12.0, workers: int = 0) -> dict:
+    """The FP64 CPU oracle's Hessian-vector products on the same workload, one process per
+    host core (spawned, so safe after CUDA has started), all timed together over a bounded
+    sample; the rate is the sum of the processes' rates."""
+    import multiprocessing as mp
+    if workers <= 0:
+        try:
+            workers = len(os.sched_getaffinity(0))      # the cores this process may run on
+        except (AttributeError, OSError):
+            workers = os.cpu_count() or 1
+    n = max(1, min(workers, 32))
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(M, seconds, 77 + i, barrier, queue)) for i in range(n)]
+    for pr in procs:
+        pr.start()
+    res = []
+    try:
+        for _ in procs:
+            res.append(queue.get(timeout=seconds + 400))
+    except Exception as ex:  # a worker died without reporting
+        res.append(f"no result: {type(ex).__name__}")
+    bad = [r for r in res if isinstance(r, str)]
+    if bad:
+        barrier.abort()
+    for pr in procs:
+        pr.join(timeout=30)
+        if pr.is_alive():
+            pr.terminate()
+            pr.join()
+    if bad:
+        return {"error": bad[0], "kind": "oracle", "cores": n}
+    done = sum(d for d, _ in res)
+    el = max(e for _, e in res)
+    return {"value": sum(d / e for d, e in res), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{done} FP64 oracle Hessian-vector products at {M}^3 on {n} processes "
+                      f"(~{el:.1f} s each, numpy, 1 thread per process)"}
 
 
 def run_reference(args, rank: int):
