@@ -13,7 +13,7 @@ struct ImexState {
     double bnorm2;       // ||b_j||^2 of the last iterate
     long long newton;    // Newton steps summed
     int it;              // iterations completed
-    int done;            // 0 running, 1 converged, 2 iteration cap, 3 non-finite
+    int done;            // 0 running, 1 converged, 2 iteration cap, 3 non-finite, 4 stalled
     int final_src;       // which B buffer holds b_{j-1} of the returned iterate
     int pad;
     double best2;        // smallest (eta residual)^2 seen by the stall test, and its iteration
@@ -135,15 +135,15 @@ __global__ void k_secular(SecArgs<T> a) {
         double res = sqrt(fmax(a.res[0], 0.0)) / a.eta;
         bool bad = !isfinite(res) || !isfinite(a.res[1]);
         const bool stall = stall_update(a.stall, j, a.res[0], best2, best_it);
-        bool conv = res < a.eps_abs || res < a.eps_rel_abs || stall;
-        if (bad || conv || j >= a.max_iter) {
+        const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+        if (bad || conv || stall || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;
                 st->bnorm2 = a.res[1];
                 st->final_lam = lam_prev;
                 st->final_src = (j - 1) & 1;
                 st->it = j;
-                st->done = bad ? 3 : (conv ? 1 : 2);
+                st->done = bad ? 3 : conv ? 1 : stall ? 4 : 2;
             }
             return;
         }

@@ -185,13 +185,20 @@ struct lb_ctx {
         const double nn = (double)p.n();
         info->iterations = hs.it;
         info->converged = hs.done == 1;
+        info->stalled = hs.done == 4;
         info->residual = hs.residual;
+        info->rel_residual = gnorm > 0.0 ? hs.residual / gnorm : hs.residual;
         info->lambda = hs.final_lam;
         info->dnorm = std::sqrt(dd[0] / nn);
         info->model_value = gd[0] / nn + 0.5 * dhd[0] / nn;
         info->newton_steps = hs.newton;
         if (hs.done == 3) { err = "lb_tr_subproblem: non-finite residual"; return LB_ERR_NONFINITE; }
         if (hs.done == 2) { err = "lb_tr_subproblem: iteration cap reached"; return LB_ERR_NOCONV; }
+        if (hs.done == 4) {
+            err = "lb_tr_subproblem: stalled (no progress in " + std::to_string(p.stall_k()) +
+                  " checked iterations) at residual " + std::to_string(hs.residual);
+            return LB_ERR_NOCONV;
+        }
         return LB_OK;
     }
 

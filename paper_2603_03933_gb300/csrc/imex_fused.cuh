@@ -175,15 +175,15 @@ __global__ void __launch_bounds__(zf_nt(M, TPC)) k_imex_zfused(ZfArgs<T> a) {
         const bool bad = !isfinite(res) || !isfinite(sums[1]);
         const bool stall = stall_update(a.stall, j, sums[0], best2, best_it);
         if (blockIdx.x == 0 && threadIdx.x == 0) { st->best2 = best2; st->best_it = best_it; }
-        const bool conv = res < a.eps_abs || res < a.eps_rel_abs || stall;
-        if (bad || conv || j >= a.max_iter) {
+        const bool conv = res < a.eps_abs || res < a.eps_rel_abs;
+        if (bad || conv || stall || j >= a.max_iter) {
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 st->residual = res;
                 st->bnorm2 = sums[1];
                 st->final_lam = lam_prev;
                 st->final_src = (j - 1) & 1;
                 st->it = j;
-                st->done = bad ? 3 : (conv ? 1 : 2);
+                st->done = bad ? 3 : conv ? 1 : stall ? 4 : 2;
             }
             return;
         }
@@ -437,15 +437,15 @@ __global__ void __launch_bounds__(zl_nt(M, TPC), TPC == 1 ? 4 : 1) k_imex_lines(
             int best_it = s_best_it;
             const bool stall = stall_update(a.stall, j, (double)res2, best2, best_it);
             if (blockIdx.x == 0) { st->best2 = best2; st->best_it = best_it; }
-            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2 || stall;
-            if (bad || conv || j >= a.max_iter) {
+            const bool conv = res2 < a.t_thr_abs2 || res2 < a.t_thr_rel2;
+            if (bad || conv || stall || j >= a.max_iter) {
                 if (blockIdx.x == 0) {
                     st->residual = (double)(sqrt(res2 > (T)0 ? res2 : (T)0) / eta);
                     st->bnorm2 = (double)bn2;
                     st->final_lam = s_lamp;
                     st->final_src = (j - 1) & 1;
                     st->it = j;
-                    st->done = bad ? 3 : (conv ? 1 : 2);
+                    st->done = bad ? 3 : conv ? 1 : stall ? 4 : 2;
                 }
                 act = ACT_RETURN;
             }

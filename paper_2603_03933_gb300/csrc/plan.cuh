@@ -35,6 +35,11 @@ template <typename T>
 class Plan {
 public:
     using C = cplx<T>;
+    // The IMEX residual is ||b_{j-1} - b_j|| / eta; in float it stops falling at the rounding
+    // level of b, which can lie above the requested tolerance.  The float path therefore
+    // also ends, reported as stalled (not converged), after 512 checked iterations without
+    // progress (stall_update); 0 in double: the paper's tests alone.
+    static int stall_k() { return sizeof(T) == 4 ? 512 : 0; }
     Plan() = default;
     ~Plan();
     int init(int dim, int m, const double box[3], double xi, double tau, double gamma, std::string& err);
@@ -140,11 +145,7 @@ private:
     long long budget_ = kDefaultBudget;
     // imex parameters of the current solve
     double r_ = 0, eps_abs_ = 0, eps_rel_abs_ = 0, rtol_ = 0, steptol_ = 0;
-    // The IMEX residual is ||b_{j-1} - b_j|| / eta; in float it stops falling at the rounding
-    // level of b, which can lie above the requested tolerance.  The float path therefore
-    // also ends after 512 checked iterations without progress (stall_update); 0 in double:
-    // the paper's tests alone.
-    static int stall_k() { return sizeof(T) == 4 ? 512 : 0; }
+
     int max_iter_ = 0;
 
     // device memory
