@@ -88,7 +88,7 @@ bool write_checkpoint(const std::string& path, const TrCheckpoint& c, const doub
     head.push_back((char)((dict.size() >> 8) & 0xff));
     head += dict;
     if (!write_file(path + ".npy", head, field, (size_t)count * sizeof(double), err)) return false;
-    char js[1024];
+    char js[2048];
     auto num = [](double x) {
         if (std::isnan(x)) return std::string("NaN");
         char b[40];
@@ -96,12 +96,17 @@ bool write_checkpoint(const std::string& path, const TrCheckpoint& c, const doub
         return std::string(b);
     };
     std::snprintf(js, sizeof(js),
-                  "{\"format\": 1, \"dim\": %d, \"n\": %d, \"j\": %d, \"r\": %s, \"nu\": %s, \"mu\": %s, "
+                  "{\"format\": 2, \"dim\": %d, \"n\": %d, \"j\": %d, \"r\": %s, \"nu\": %s, \"mu\": %s, "
                   "\"rho_prev\": %s, \"have_rho\": %d, \"random_next\": %d, \"rstream\": %u, \"accepted\": %d, "
-                  "\"contracted\": %d, \"shrunk\": %d, \"randomized\": %d, \"inner\": %lld, \"g1_min\": %s}\n",
+                  "\"contracted\": %d, \"shrunk\": %d, \"randomized\": %d, \"inner\": %lld, \"g1_min\": %s, "
+                  "\"sub_stalled\": %d, \"sub_capped\": %d, \"sub_worst_rel_res\": %s, \"box_x\": %s, "
+                  "\"box_y\": %s, \"box_z\": %s, \"xi\": %s, \"tau\": %s, \"gamma\": %s, \"eta\": %s, "
+                  "\"precision\": %d}\n",
                   c.dim, c.n, c.j, num(c.r).c_str(), num(c.nu).c_str(), num(c.mu).c_str(), num(c.rho_prev).c_str(),
                   c.have_rho, c.random_next, c.rstream, c.accepted, c.contracted, c.shrunk, c.randomized, c.inner,
-                  num(c.g1_min).c_str());
+                  num(c.g1_min).c_str(), c.sub_stalled, c.sub_capped, num(c.sub_worst_rel_res).c_str(),
+                  num(c.box[0]).c_str(), num(c.box[1]).c_str(), num(c.box[2]).c_str(), num(c.xi).c_str(),
+                  num(c.tau).c_str(), num(c.gamma).c_str(), num(c.eta).c_str(), c.precision);
     return write_file(path + ".json", js, nullptr, 0, err);
 }
 
@@ -109,17 +114,28 @@ bool read_checkpoint(const std::string& path, TrCheckpoint& c, std::vector<doubl
     if (!little_endian()) { err = "checkpoint: big-endian hosts are not supported"; return false; }
     std::string js;
     if (!read_all(path + ".json", js, err)) return false;
-    double v[17];
-    const char* keys[17] = {"format", "dim", "n", "j", "r", "nu", "mu", "rho_prev", "have_rho", "random_next",
-                            "rstream", "accepted", "contracted", "shrunk", "randomized", "inner", "g1_min"};
-    for (int i = 0; i < 17; ++i)
+    constexpr int NK = 28;
+    double v[NK];
+    const char* keys[NK] = {"format", "dim", "n", "j", "r", "nu", "mu", "rho_prev", "have_rho", "random_next",
+                            "rstream", "accepted", "contracted", "shrunk", "randomized", "inner", "g1_min",
+                            "sub_stalled", "sub_capped", "sub_worst_rel_res", "box_x", "box_y", "box_z", "xi",
+                            "tau", "gamma", "eta", "precision"};
+    if (!json_number(js, keys[0], v[0])) { err = "checkpoint: no \"format\" in " + path + ".json"; return false; }
+    if (v[0] != 2.0) {
+        err = "checkpoint: " + path + ".json has format " + std::to_string((int)v[0]) +
+              ", not 2 (an older file does not record the problem it belongs to)";
+        return false;
+    }
+    for (int i = 1; i < NK; ++i)
         if (!json_number(js, keys[i], v[i])) { err = std::string("checkpoint: no \"") + keys[i] + "\" in " + path + ".json"; return false; }
-    if (v[0] != 1.0) { err = "checkpoint: unknown format in " + path + ".json"; return false; }
     c.dim = (int)v[1]; c.n = (int)v[2]; c.j = (int)v[3];
     c.r = v[4]; c.nu = v[5]; c.mu = v[6]; c.rho_prev = v[7];
     c.have_rho = (int)v[8]; c.random_next = (int)v[9]; c.rstream = (unsigned)v[10];
     c.accepted = (int)v[11]; c.contracted = (int)v[12]; c.shrunk = (int)v[13]; c.randomized = (int)v[14];
     c.inner = (long long)v[15]; c.g1_min = v[16];
+    c.sub_stalled = (int)v[17]; c.sub_capped = (int)v[18]; c.sub_worst_rel_res = v[19];
+    c.box[0] = v[20]; c.box[1] = v[21]; c.box[2] = v[22];
+    c.xi = v[23]; c.tau = v[24]; c.gamma = v[25]; c.eta = v[26]; c.precision = (int)v[27];
     if (c.dim < 1 || c.dim > 3 || c.n < 1) { err = "checkpoint: bad grid in " + path + ".json"; return false; }
     std::string raw;
     if (!read_all(path + ".npy", raw, err)) return false;
@@ -144,6 +160,22 @@ bool read_checkpoint(const std::string& path, TrCheckpoint& c, std::vector<doubl
     }
     field.resize((size_t)count);
     std::memcpy(field.data(), raw.data() + 10 + hl, (size_t)count * sizeof(double));
+    return true;
+}
+
+bool checkpoint_matches(const TrCheckpoint& c, const TrCheckpoint& want, std::string& err) {
+    auto bad = [&](const char* what) {
+        err = std::string("checkpoint: written for another ") + what;
+        return false;
+    };
+    if (c.dim != want.dim || c.n != want.n) return bad("grid");
+    for (int a = 0; a < want.dim; ++a)
+        if (c.box[a] != want.box[a]) return bad("box");
+    if (c.xi != want.xi) return bad("xi");
+    if (c.tau != want.tau) return bad("tau");
+    if (c.gamma != want.gamma) return bad("gamma");
+    if (c.precision != want.precision) return bad("precision");
+    if (c.eta != want.eta) return bad("subproblem step eta");
     return true;
 }
 

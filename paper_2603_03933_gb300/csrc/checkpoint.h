@@ -28,7 +28,19 @@ struct TrCheckpoint {
     int accepted = 0, contracted = 0, shrunk = 0, randomized = 0;
     long long inner = 0;
     double g1_min = 0.0;        // NaN if never measured
+    int sub_stalled = 0, sub_capped = 0;
+    double sub_worst_rel_res = 0.0;
+    // the problem and the solver settings the state belongs to: a resume with other values
+    // would carry r, nu, mu and the previous ratio into a different problem
+    double box[3] = {0.0, 0.0, 0.0};
+    double xi = 0.0, tau = 0.0, gamma = 0.0, eta = 0.0;
+    int precision = 0;          // lb_precision of the context
 };
+
+// true if `c` (read from a file) was written for the problem and settings of `want`
+// (grid, box lengths, xi, tau, gamma, precision and the subproblem step eta, compared
+// exactly: they are written with 17 digits); false with a message naming the first mismatch
+bool checkpoint_matches(const TrCheckpoint& c, const TrCheckpoint& want, std::string& err);
 
 // false with a message on any I/O error
 bool write_checkpoint(const std::string& path, const TrCheckpoint& c, const double* field, long long count,

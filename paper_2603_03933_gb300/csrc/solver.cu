@@ -287,13 +287,22 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
     lb_status result = LB_ERR_NOCONV;
     int j = 0, j0 = 0;
     double E = 0.0, gmax = 0.0;
+    // the problem and settings a checkpoint of this solve belongs to
+    auto ckpt_identity = [&]() {
+        TrCheckpoint c;
+        c.dim = prob.dim; c.n = prob.n;
+        for (int a = 0; a < 3; ++a) c.box[a] = a < prob.dim ? prob.box[a] : 0.0;
+        c.xi = prob.xi; c.tau = prob.tau; c.gamma = prob.gamma;
+        c.eta = o.sub.eta; c.precision = (int)prec;
+        return c;
+    };
     if (o.resume && o.checkpoint_path) {
         TrCheckpoint c;
         std::vector<double> field;
         std::string e;
         if (!read_checkpoint(o.checkpoint_path, c, field, e)) { err = "lb_imex_tr_solve: " + e; return LB_ERR_INVALID_ARG; }
-        if (c.dim != prob.dim || c.n != prob.n || (long long)field.size() != P.n()) {
-            err = "lb_imex_tr_solve: the checkpoint holds another grid";
+        if (!checkpoint_matches(c, ckpt_identity(), e) || (long long)field.size() != P.n()) {
+            err = "lb_imex_tr_solve: " + (e.empty() ? std::string("the checkpoint holds another grid") : e);
             return LB_ERR_INVALID_ARG;
         }
         cudaMemcpyAsync(v, field.data(), field.size() * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -309,6 +318,9 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
         info->randomized = c.randomized;
         info->inner = c.inner;
         info->g1_min = c.g1_min;
+        info->sub_stalled = c.sub_stalled;
+        info->sub_capped = c.sub_capped;
+        info->sub_worst_rel_res = c.sub_worst_rel_res;
     }
     // the state carried into outer iteration `next`, written to the checkpoint files
     auto checkpoint = [&](int next) -> lb_status {
@@ -316,12 +328,14 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
         cudaMemcpyAsync(field.data(), v, field.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaError_t ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) { err = std::string("lb_imex_tr_solve: ") + cudaGetErrorString(ce); return LB_ERR_CUDA; }
-        TrCheckpoint c;
-        c.dim = prob.dim; c.n = prob.n; c.j = next;
+        TrCheckpoint c = ckpt_identity();
+        c.j = next;
         c.r = S.r; c.nu = S.nu; c.mu = S.mu; c.rho_prev = S.rho_prev; c.have_rho = S.have_rho ? 1 : 0;
         c.random_next = random_next ? 1 : 0; c.rstream = rstream;
         c.accepted = info->accepted; c.contracted = info->contracted; c.shrunk = info->shrunk;
         c.randomized = info->randomized; c.inner = info->inner; c.g1_min = info->g1_min;
+        c.sub_stalled = info->sub_stalled; c.sub_capped = info->sub_capped;
+        c.sub_worst_rel_res = info->sub_worst_rel_res;
         std::string e;
         if (!write_checkpoint(o.checkpoint_path, c, field.data(), (long long)field.size(), e)) {
             err = "lb_imex_tr_solve: " + e;
@@ -393,6 +407,11 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
         random_next = false;
         if (ss != LB_OK && ss != LB_ERR_NOCONV) return ss;
         info->inner += si.iterations;
+        if (!si.converged) {
+            if (si.stalled) ++info->sub_stalled;
+            else ++info->sub_capped;
+            info->sub_worst_rel_res = std::max(info->sub_worst_rel_res, si.rel_residual);
+        }
         // project the step onto zero mean in FP64 (P of §3): a float step carries a rounding
         // mean that would otherwise accumulate in the iterate
         P.phys_reduce(R_SUM_SUMSQ, sd, nullptr, S_RED1, s);
@@ -473,8 +492,10 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
             std::fprintf(stderr,
                          "{\"j\": %d, \"E\": %.15g, \"gmax\": %.3e, \"r\": %.6g, \"nu\": %.6g, \"mu\": %.6g, "
                          "\"lambda\": %.6g, \"snorm\": %.6g, \"rho\": %.6g, \"inner\": %d, \"sub_status\": %d, "
+                         "\"sub_stalled\": %d, \"sub_rel_res\": %.3e, "
                          "\"acc\": %d, \"con\": %d, \"shr\": %d}\n",
-                         j, E, gmax, S.r, S.nu, S.mu, lam, sn, rho, si.iterations, (int)ss, info->accepted,
+                         j, E, gmax, S.r, S.nu, S.mu, lam, sn, rho, si.iterations, (int)ss, si.stalled, si.rel_residual,
+                         info->accepted,
                          info->contracted, info->shrunk);
         if (o.checkpoint_path && o.checkpoint_every > 0 && (j + 1) % o.checkpoint_every == 0)
             if ((st = checkpoint(j + 1))) return st;
