@@ -6,7 +6,9 @@
 // This entry point serves them: it needs no lb_ctx, and its scratch (one half
 // spectrum, the reduction partials, the twiddle and wavenumber tables) lives in a
 // file-scope __device__ array of fixed size.  The caller passes only the problem, the
-// input fields and the output field.
+// input fields and the output field.  Every call writes its tables into that array with
+// a small kernel on the caller's stream, so after the first call on a device (which
+// resolves the array's address) a call only enqueues kernels.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -89,6 +91,32 @@ cudaError_t device_setup(int dev, unsigned char** base) {
     return cudaSuccess;
 }
 
+// The twiddles W_M^j = exp(-2 pi i j / M) and the per-axis |Bk|^2 terms (2 pi k / L_a)^2
+// (signed wavenumber k of index i) of one problem, evaluated in double and rounded to T;
+// also resets the reduction ticket.  One block; m <= 512.
+template <typename T>
+__global__ void k_noalloc_tables(cplx<T>* tw, T* qt, unsigned* ticket, int m, int dim, double lx, double ly,
+                                 double lz) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double len[3] = {lx, ly, lz};
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)j / (double)m, &sn, &cs);
+        tw[j] = mk<T>((T)cs, (T)sn);
+    }
+    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) {
+        const int ax = i / m, idx = i % m;
+        const int k = idx < m / 2 ? idx : idx - m;
+        double q = 0.0;
+        if (ax < dim) {
+            const double c = two_pi / len[ax];
+            q = c * c * (double)k * (double)k;
+        }
+        qt[i] = (T)q;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 struct Layout {
     size_t spec, tw, qtab, partials, result, ticket, total;
 };
@@ -125,28 +153,10 @@ lb_status run(const lb_problem& pr, const T* phi, const T* v, T* hv, cudaStream_
     double* result = reinterpret_cast<double*>(base + L.result);
     unsigned* ticket = reinterpret_cast<unsigned*>(base + L.ticket);
 
-    // tables of this problem (host arrays on the stack; M <= 512)
-    C htw[512];
-    T hq[3 * 512];
-    const long double pi = 3.141592653589793238462643383279502884L;
-    for (int j = 0; j < m; ++j) {
-        long double ang = -2.0L * pi * (long double)j / (long double)m;
-        htw[j] = mk<T>((T)cosl(ang), (T)sinl(ang));
-    }
-    for (int i = 0; i < 3 * m; ++i) hq[i] = (T)0;
-    for (int ax = 0; ax < dim; ++ax) {
-        long double c = 2.0L * pi / (long double)pr.box[ax];
-        for (int i = 0; i < m; ++i) {
-            int k = i < h ? i : i - m;
-            hq[ax * m + i] = (T)(c * c * (long double)k * (long double)k);
-        }
-    }
-    // cudaMemcpyAsync from pageable host memory returns once the source has been
-    // consumed, so the stack arrays may go out of scope afterwards
-    if (cudaMemcpyAsync(tw, htw, sizeof(C) * m, cudaMemcpyHostToDevice, s) != cudaSuccess) return LB_ERR_CUDA;
-    if (cudaMemcpyAsync(qt, hq, sizeof(T) * 3 * m, cudaMemcpyHostToDevice, s) != cudaSuccess) return LB_ERR_CUDA;
-    // the reduction ticket must start at zero (the shared array keeps the last call's state)
-    if (cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) != cudaSuccess) return LB_ERR_CUDA;
+    // tables of this problem and the reduction ticket, written on the device in stream
+    // order (the shared array keeps the last call's contents, so the ticket must be reset)
+    k_noalloc_tables<T><<<1, 512, 0, s>>>(tw, qt, ticket, m, dim, pr.box[0], pr.box[1], dim == 3 ? pr.box[2] : 1.0);
+    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
 
     Model<T> model;
     model.tau = (T)pr.tau; model.gamma = (T)pr.gamma; model.eta = (T)0.1;
