@@ -138,12 +138,16 @@ typedef struct {
 
 typedef struct {
     int iterations;        /* IMEX iterations performed */
-    int converged;         /* 1 if the residual test passed */
+    int converged;         /* 1 if the residual test of Algorithm 3 (eps_sub or rel_tol) passed */
     double residual;       /* ||g + (H + lambda I) d|| of the returned d */
     double lambda;         /* Lagrange multiplier of the returned d */
     double dnorm;          /* ||d|| */
     double model_value;    /* f(d) = <g,d> + <d,Hd>/2 (eq. tr_subproblem) */
     long long newton_steps;/* Newton steps spent on the secular equation, summed */
+    double rel_residual;   /* residual / ||g|| */
+    int stalled;           /* 1 if the LB_MIXED iteration ended because its residual stopped
+                              falling (512 checked iterations without a 2 % drop of the squared
+                              residual) before reaching the tolerance; converged is then 0 */
 } lb_sub_info;
 
 /* Fill `o` with the paper's values (eta 0.1, eps_sub 1e-13) and max_iter 20000. */
@@ -161,7 +165,9 @@ void lb_default_sub_opts(lb_sub_opts *o);
  *       randomised start of the hard-case remark, which must satisfy ||d0|| <= r).
  *   d   [out] device field: the returned d_{k+1}.
  *   info[out] host struct (may be NULL).
- * Returns LB_ERR_NOCONV (with d holding the last iterate) if max_iter is reached.
+ * Returns LB_ERR_NOCONV (with d holding the last iterate) if max_iter is reached, and in
+ * LB_MIXED also when the float iteration stalls above the tolerance (info->stalled = 1;
+ * info->residual and info->rel_residual give the residual reached).
  */
 lb_status lb_tr_subproblem(lb_ctx *ctx, const void *phi, const void *g, double r,
                            const void *d0, const lb_sub_opts *opts, void *d,
@@ -221,8 +227,11 @@ typedef struct {
      * every checkpoint_every-th outer iteration.  If resume != 0, the solve starts from
      * that checkpoint instead of phi_inout and repeats the remaining iterations exactly;
      * max_outer still counts from the first iteration of the original solve.  The path
-     * is borrowed for the duration of the call.  Errors: LB_ERR_INVALID_ARG when a file
-     * cannot be written or read, or holds another grid. */
+     * is borrowed for the duration of the call.  The files also record the grid, the box
+     * lengths, xi, tau, gamma, the precision and the subproblem step eta; a resume refuses a
+     * checkpoint whose values differ from the context's and the options'.  Errors:
+     * LB_ERR_INVALID_ARG when a file cannot be written or read, or belongs to another
+     * problem. */
     const char *checkpoint_path;
     int checkpoint_every;
     int resume;
@@ -238,6 +247,9 @@ typedef struct {
     int status;          /* lb_status of the solve */
     int randomized;      /* subproblems started from a random point of the ball */
     double g1_min;       /* smallest |g^(1)| seen by the nearly-hard test (NaN if never run) */
+    int sub_stalled;     /* subproblems that ended stalled above their tolerance (LB_MIXED) */
+    int sub_capped;      /* subproblems that ended at the iteration cap */
+    double sub_worst_rel_res; /* largest residual / ||g|| among those (0 if none) */
 } lb_tr_info;
 
 void lb_default_tr_opts(lb_tr_opts *o);
@@ -304,8 +316,9 @@ lb_status lb_sis_solve(lb_ctx *ctx, double *phi_inout, const lb_sis_opts *opts, 
  * attributes (once per device, with that device current); make that first call
  * before any stream capture.  Every call shares the one scratch array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be serialised
- * by the caller.  Asynchronous on `stream` apart from two small host-to-device table
- * copies.
+ * by the caller.  Asynchronous on `stream`: each call writes its tables into the scratch
+ * with a small kernel and enqueues the transform kernels; it neither copies from the host
+ * nor synchronises.
  */
 lb_status lb_hessvec_noalloc(const lb_problem *prob, lb_precision prec, const void *phi, const void *v,
                              void *hv, lb_stream stream);

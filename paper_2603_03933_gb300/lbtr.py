@@ -43,7 +43,7 @@ class lb_sub_opts(ctypes.Structure):
 class lb_sub_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("dnorm", ctypes.c_double), ("model_value", ctypes.c_double),
-                ("newton_steps", ctypes.c_longlong)]
+                ("newton_steps", ctypes.c_longlong), ("rel_residual", ctypes.c_double), ("stalled", ctypes.c_int)]
 
 
 class lb_eig_opts(ctypes.Structure):
@@ -70,7 +70,8 @@ class lb_tr_info(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int), ("inner", ctypes.c_longlong), ("accepted", ctypes.c_int),
                 ("contracted", ctypes.c_int), ("shrunk", ctypes.c_int), ("energy", ctypes.c_double),
                 ("gmax", ctypes.c_double), ("lambda_min", ctypes.c_double), ("status", ctypes.c_int),
-                ("randomized", ctypes.c_int), ("g1_min", ctypes.c_double)]
+                ("randomized", ctypes.c_int), ("g1_min", ctypes.c_double), ("sub_stalled", ctypes.c_int),
+                ("sub_capped", ctypes.c_int), ("sub_worst_rel_res", ctypes.c_double)]
 
 
 class lb_sis_opts(ctypes.Structure):
@@ -283,7 +284,8 @@ def lb_tr_subproblem(ctx: Context, phi, g, r: float, d, d0=None, opts: lb_sub_op
         _check(ctx, st, "lb_tr_subproblem")
     return {"iterations": info.iterations, "converged": bool(info.converged), "residual": info.residual,
             "lambda": info.lambda_, "dnorm": info.dnorm, "model_value": info.model_value,
-            "newton_steps": info.newton_steps, "status": st}
+            "newton_steps": info.newton_steps, "rel_residual": info.rel_residual,
+            "stalled": bool(info.stalled), "status": st}
 
 
 def default_eig_opts() -> lb_eig_opts:
@@ -324,7 +326,9 @@ def lb_imex_tr_solve(ctx: Context, phi64, opts: lb_tr_opts | None = None, stream
     return {"outer": info.outer, "inner": info.inner, "accepted": info.accepted, "contracted": info.contracted,
             "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
             "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": st,
-            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None}
+            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None,
+            "sub_stalled": info.sub_stalled, "sub_capped": info.sub_capped,
+            "sub_worst_rel_res": info.sub_worst_rel_res}
 
 
 def default_sis_opts() -> lb_sis_opts:
@@ -450,7 +454,9 @@ def _tr_info_dict(info: lb_tr_info) -> dict:
     return {"outer": info.outer, "inner": info.inner, "accepted": info.accepted, "contracted": info.contracted,
             "shrunk": info.shrunk, "energy": info.energy, "gmax": info.gmax,
             "lambda_min": info.lambda_min if not math.isnan(info.lambda_min) else None, "status": info.status,
-            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None}
+            "randomized": info.randomized, "g1_min": info.g1_min if not math.isnan(info.g1_min) else None,
+            "sub_stalled": info.sub_stalled, "sub_capped": info.sub_capped,
+            "sub_worst_rel_res": info.sub_worst_rel_res}
 
 
 def lb_batch_tr_solve(batch: Batch, phis, opts: lb_tr_opts | None = None, nthreads: int = 0, stream=None,
