@@ -37,18 +37,13 @@ L2_BYTES = 129 * 1024 * 1024
 # ncu DRAM traffic per launch of a kernel class, with the hash of the kernel sources it
 # was captured from (a traffic figure is reported only while those sources match).
 TRAFFIC = {
-    # k_plane_fwd<float,128,XF_HVPMEAN>, k_lines<float,128,C_LAM>, k_plane_inv<float,128,XI_HVP>
-    "xfwd": (16820224, "b56d0e19fe0694b5"),
-    "col_inner": (8549632, "b56d0e19fe0694b5"),
-    "xinv": (25326848, "b56d0e19fe0694b5"),
+    # k_hvp_fused<float> (the whole 128^3 product, one launch)
+    "xfwd": (None, ""),
 }
 
 
-# nominal FP64 (CUDA-core) rate of GB300, TFLOP/s: the bound of the FP64 path
-FP64_PEAK_TFLOPS = 1.25
-
 # the sources that define the HVP kernels (their DRAM traffic is keyed to these)
-HVP_KERNEL_SOURCES = ("common.cuh", "fft_core.cuh", "reduce.cuh", "passes.cuh", "planes.cuh", "lines.cuh")
+HVP_KERNEL_SOURCES = ("common.cuh", "fft_core.cuh", "reduce.cuh", "passes.cuh", "hvp3d.cuh")
 
 
 def csrc_hash() -> str:
@@ -505,15 +500,20 @@ def main():
     ms, nl, by = prof[dom]
     achieved = (by / nl) / (ms / nl / 1e3) / 1e9
     tr = TRAFFIC.get(dom)
-    traffic = tr[0] if (tr and tr[1] == csrc_hash()) else None
+    traffic = tr[0] if (tr and tr[0] is not None and tr[1] == csrc_hash()) else None
+    # headline: the whole Hessian-vector product against its algorithmic bytes (read v and
+    # phi, write Hv: 12 N bytes in float), timed over the timed region above
     hvp_time = dt / (args.batch * args.steps)
     hvp_alg = 3 * field_bytes
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": peaks["source"],
-                "hvp": {"alg_bytes": hvp_alg, "us": hvp_time * 1e6,
-                        "achieved_gbs": hvp_alg / hvp_time / 1e9,
-                        "frac": hvp_alg / hvp_time / 1e9 / peaks["hbm_gbs"]},
+    hvp_gbs = hvp_alg / hvp_time / 1e9
+    traffic_hvp = (sum(TRAFFIC[k][0] for k in TRAFFIC)
+                   if all(TRAFFIC[k][0] is not None and TRAFFIC[k][1] == csrc_hash() for k in TRAFFIC) else None)
+    roofline = {"bound": "hbm", "kernel": "hvp: " + " + ".join(k for k in prof if prof[k][1] > 0),
+                "achieved": hvp_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hvp_gbs / peaks["hbm_gbs"], "traffic": traffic_hvp, "peak_source": peaks["source"],
+                "alg_bytes_per_hvp": hvp_alg, "us_per_hvp": hvp_time * 1e6,
+                "dominant": {"kernel": dom, "achieved": achieved, "frac": achieved / peaks["hbm_gbs"],
+                             "traffic": traffic},
                 "per_kernel": {k: {"launches": v[1], "avg_us": 1e3 * v[0] / v[1],
                                    "alg_gbs": (v[2] / v[1]) / (v[0] / v[1] / 1e3) / 1e9,
                                    "share": v[0] / sum(x[0] for x in prof.values())}
@@ -525,14 +525,16 @@ def main():
     dt64 = time_hvp(lbtr, ctx64, pool64, 4, 3, 1, 1)
     fp64 = {"value": 12 / dt64, "unit": UNIT, "us_per_hvp": dt64 / 12 * 1e6}
     # the FP64 path is bound by FP64 arithmetic: algorithmic flops of one HVP (a real 3D
-    # FFT each way, 2.5 N log2 N each, plus ~10 N pointwise) against GB300's nominal FP64 rate
+    # FFT each way, 2.5 N log2 N each, plus ~10 N pointwise) against the FP64 FMA rate
+    # measured on this GPU by the library's FMA-loop probe
     try:
         nn = float(w.n_points)
         flops64 = 5.0 * nn * math.log2(nn) + 10.0 * nn
         ach64 = flops64 / (dt64 / 12) / 1e12
-        fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": ach64 / FP64_PEAK_TFLOPS, "flops_per_hvp": flops64,
-                            "peak_source": "nominal GB300 FP64 rate"}
+        peak64 = lbtr.lb_measure_fp64_rate()
+        fp64["roofline"] = {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                            "frac": ach64 / peak64, "flops_per_hvp": flops64,
+                            "peak_source": "measured: FP64 FMA loop (lb_measure_fp64_rate), this run"}
     except Exception as ex:  # report, do not hide
         fp64["roofline"] = {"error": str(ex)}
     del pool64, ctx64
@@ -599,9 +601,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_hvp_rate(M)
 
-    # kernels per HVP: x/y plane pass, z line pass, inverse plane pass (3D 32^3-128^3); else
-    # x rows, y lines, z lines (with Lambda), y lines, inverse x rows
-    launches_per_hvp = 3 if 32 <= M <= 128 else 5
+    # kernels per HVP: one cooperative launch at 128^3 (float); x/y plane pass, z line pass,
+    # inverse plane pass at 32^3-64^3; else x rows, y lines, z lines (with Lambda), y lines,
+    # inverse x rows
+    launches_per_hvp = 1 if M == 128 else 3 if 32 <= M <= 128 else 5
     sweep = time_sweep(lbtr, rank, world, args.sweep_instances) if args.sweep_instances > 0 else None
     sweep_solve = None
     if args.sweep_solve_instances > 0:

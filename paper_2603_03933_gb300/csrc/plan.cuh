@@ -169,6 +169,8 @@ private:
     cudaError_t launch_err_ = cudaSuccess;
     Prof* prof_ = nullptr;
     bool use_planes_ = false;
+    bool hvp3_ = false;       // 3D 128^3 float products take the kernels of hvp3d.cuh
+    int hvp3_grid_ = 0;       // CTAs of the fused cooperative product (0: three kernels)
     int ln_grid_cap_ = 0;     // persistent grid of the pipelined column passes (0: not used)
     int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
     size_t zf_smem_ = 0;

@@ -8,6 +8,7 @@
 #include "lines.cuh"
 #include "rows.cuh"
 #include "imex_fused.cuh"
+#include "hvp3d.cuh"
 
 namespace lbtr {
 
@@ -182,6 +183,20 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     LB_SWITCH_M(m_, ea = set_smem_attrs<T, M>());
     if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
     use_planes_ = (dim_ == 3 && m_ >= 32 && m_ <= 128);
+    hvp3_ = (sizeof(T) == 4 && dim_ == 3 && m_ == H3::M);
+    if (hvp3_) {
+        ea = cudaFuncSetAttribute((const void*)k_hvp_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)H3::FSMEM);
+        if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+        // the fused kernel needs every CTA resident at once (cooperative launch); without
+        // that, products take the plane kernels below
+        int per = 0;
+        ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hvp_fused<T>, H3::NT, H3::FSMEM);
+        if (ea != cudaSuccess) { err = std::string("cudaOccupancyMaxActiveBlocksPerMultiprocessor: ") + cudaGetErrorString(ea); return 6; }
+        int coop = 0;
+        LB_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        hvp3_grid_ = (coop && per > 0) ? nsm * per : 0;
+    }
     if (use_planes_) {
         LB_SWITCH_M(m_, ea = set_plane_attrs<T, M>());
         if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
@@ -530,6 +545,25 @@ void Plan<T>::mid_outer(int mode, C* spec, const T* phi, const T* g, T scale, cu
 }
 
 template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cudaStream_t s) {
+    if (hvp3_grid_ > 0) {
+        Hvp3Args<T> a;
+        a.v = v; a.phi = phi; a.hv = hv; a.spec = d_work_; a.tw = d_tw_; a.qtab = d_qtab_;
+        a.model = model_;
+        a.partials = d_partials_;
+        a.bar.count = d_bar_; a.bar.gen = d_bar_ + 32; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 64;
+        a.inv_n = 1.0 / (double)n_;
+        a.xi2 = (T)xi2_;
+        a.kscale = (T)(1.0 / (double)n_);
+        {
+            void* args[] = {&a};
+            cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+            cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_hvp_fused<T>, dim3(hvp3_grid_), dim3(H3::NT),
+                                                        args, H3::FSMEM, s);
+            if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+            if (prof_) prof_->end(K_XFWD, e0, s, 3 * fb());
+            return;
+        }
+    }
     const int inner = dim_ == 3 ? 2 : 1;
     fwd_outer(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
     cols(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0, s);

@@ -105,12 +105,16 @@ __device__ __forceinline__ void block_part(Acc<T> (&a)[NQ], double* scratch, Par
 #pragma unroll
         for (int q = 0; q < NQ; ++q) sp[q * 32 + warp] = part_of(a[q]);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // the warp totals are summed by warp 0 as a fixed shuffle tree (deterministic)
+    if (warp == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            Part<T> t = sp[q * 32];
-            for (int w = 1; w < nw; ++w) t = part_add(t, sp[q * 32 + w]);
-            out[q] = t;
+            Part<T> t;
+            if (lane < nw) t = sp[q * 32 + lane];
+            else part_zero(t);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t = part_add(t, part_shfl_down(t, off));
+            if (lane == 0) out[q] = t;
         }
     }
     __syncthreads();
