@@ -61,6 +61,8 @@ struct H3 {
     static constexpr int NLINES = NKX * M;           // 8320 z-lines
     static constexpr int NTASKS = NLINES / 4;        // four lines per warp
     // the fused kernel: one CTA of 1024 threads per SM holds either phase's shared memory
+    // (keeping the plane's F''(phi) v in shared memory from phase 1 to phase 3 was measured
+    // slower: the larger carve-out leaves less L1 for the loads of phase 1)
     static constexpr size_t FSMEM = (32 * ZWARP > SMEM ? 32 * ZWARP : SMEM);
 };
 
@@ -93,6 +95,35 @@ template <typename T> __device__ __forceinline__ void h3_pow7(cplx<T> b, cplx<T>
     w[7] = cmul(w[6], b);
 }
 
+// Grid barrier of the fused product: thread 0 of each CTA arrives with an acquire-release
+// atomic (its CTA's earlier stores published by the release), the last arrival resets the
+// count and releases the generation word, the others poll it with acquire loads.  The spin
+// is bounded by gb.budget clock cycles; on expiry the error flag is set and false returned.
+__device__ __forceinline__ bool h3_grid_sync(const GridBar& gb) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned* gen = (unsigned*)gb.gen;
+        const unsigned my_gen = ld_acquire_gpu(gen);
+        if (atom_add_acq_rel_gpu(gb.count, 1u) == gridDim.x - 1u) {
+            *gb.count = 0u;
+            red_add_release_gpu(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(gen) == my_gen) {
+                if (clock64() - t0 > gb.budget || *(volatile int*)gb.err != 0) {
+                    atomicCAS(gb.err, 0, 5);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // f''(u) = tau - gamma u + u^2 / 2 (as f2v of passes.cuh)
 template <typename T> __device__ __forceinline__ T h3_f2(const Model<T>& m, T u) {
     return m.tau + u * ((T)0.5 * u - m.gamma);
@@ -123,8 +154,9 @@ __device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsign
         for (int m = 0; m < 8; ++m) { u[m] = vr[j + 8 * m]; p[m] = pr[j + 8 * m]; }
     }
     {
-        // the thread's 16 terms of the projection sum in the working precision, then the
-        // warp's total in double-word form; warp totals are added after the hand-off barrier
+        // w = F''(phi) v, kept in shared memory for phase 3; the thread's 16 terms of the
+        // projection sum in the working precision, then the warp's total in double-word form;
+        // warp totals are added after the hand-off barrier
         T sum = (T)0;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -267,13 +299,18 @@ __device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cp
     const T qzc = __ldg(&qt[2 * M + 1]);                     // (2 pi / L_z)^2: |Bk|^2 of kz is qzc * k^2
     // forward: DFT16 over m, twiddle W_M^{i q}, transpose, DFT8 over i
     dft_r<-1, 16, T>(v);
-    C w[8], w8;                                              // W_M^{iq} (q < 8) and W_M^{8i}
-    h3_pow7<T>(twi, w);
-    w8 = cmul(w[4], w[4]);
+    {
+        // W_M^{iq}: two running products of depth 7 (q = 1..7 and q = 8..15), few registers
+        C wa = twi, wb = __ldg(&tw[(8 * i) & (M - 1)]);
+        v[8] = cmul(v[8], wb);
 #pragma unroll
-    for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], w[q]);
-#pragma unroll
-    for (int q = 8; q < 16; ++q) v[q] = cmul(v[q], cmul(w8, w[q - 8]));
+        for (int q = 1; q < 8; ++q) {
+            v[q] = cmul(v[q], wa);
+            wb = cmul(wb, twi);
+            v[q + 8] = cmul(v[q + 8], wb);
+            wa = cmul(wa, twi);
+        }
+    }
     C* tl = ts + l * G::ZTS;                                 // element (q, i) at tl[9 q + i]
 #pragma unroll
     for (int q = 0; q < 16; ++q) tl[q * 9 + i] = v[q];
@@ -300,14 +337,17 @@ __device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cp
                 v[s * 8 + b] = mk<T>(v[s * 8 + b].x * f, v[s * 8 + b].y * f);
             }
     }
-    // inverse: DFT8 over b, twiddle W_M^{-i' q}, transpose back, DFT16
+    // inverse: DFT8 over b, twiddle W_M^{-c q} (q = i + 8 s), transpose back, DFT16
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         dft_r<+1, 8, T>(&v[s * 8]);
+        // running product of W_M^{-q}, q = i + 8 s
+        const C wq1 = s ? cconj(cmul(twi, __ldg(&tw[8]))) : cconj(twi);
+        C wc = wq1;
 #pragma unroll
         for (int c = 1; c < 8; ++c) {
-            const C wq = s ? cmul(w[c], h3_w16<T>(c)) : w[c];      // W_M^{c (i + 8 s)}
-            v[s * 8 + c] = cmul(v[s * 8 + c], cconj(wq));
+            v[s * 8 + c] = cmul(v[s * 8 + c], wc);
+            wc = cmul(wc, wq1);
         }
     }
     __syncwarp();
@@ -471,20 +511,25 @@ template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_hvp_fused(Hvp3Args<T> a) {
     using G = H3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nb = gridDim.x;
-    for (int z = blockIdx.x; z < G::M; z += nb) {
-        h3_fwd_plane<T>(a, z, smem_raw);
+    const int nb = gridDim.x, z = blockIdx.x;
+    for (int zz = z; zz < G::M; zz += nb) {
+        h3_fwd_plane<T>(a, zz, smem_raw);
         __syncthreads();                                     // shared memory reused by the next plane
     }
-    if (!grid_sync(a.bar)) return;
+    if (!h3_grid_sync(a.bar)) return;
     {
-        cplx<T>* ts = reinterpret_cast<cplx<T>*>(smem_raw + (threadIdx.x >> 5) * G::ZWARP);
-        // tasks interleaved over CTAs so that every SM gets a share
-        for (int q = (threadIdx.x >> 5) * nb + blockIdx.x; q < G::NTASKS; q += 32 * nb) h3_zline_task<T>(a, q, ts);
+        // z-line tasks on the first warps of every CTA, interleaved over CTAs
+        const int warp = threadIdx.x >> 5, nw = (G::NTASKS + nb - 1) / nb;
+        const int nwork = nw < 32 ? nw : 32;
+        cplx<T>* ts = reinterpret_cast<cplx<T>*>(smem_raw + warp * G::ZWARP);
+        if (warp < nwork) {
+#pragma unroll 1
+            for (int q = warp * nb + z; q < G::NTASKS; q += nwork * nb) h3_zline_task<T>(a, q, ts);
+        }
     }
-    if (!grid_sync(a.bar)) return;
-    for (int z = blockIdx.x; z < G::M; z += nb) {
-        h3_inv_plane<T>(a, z, smem_raw);
+    if (!h3_grid_sync(a.bar)) return;
+    for (int zz = z; zz < G::M; zz += nb) {
+        h3_inv_plane<T>(a, zz, smem_raw);
         __syncthreads();
     }
 }
