@@ -79,11 +79,14 @@ def kkt_residual(p: lb.Problem, psi, g, d, lam: float) -> float:
 
 def imex_subproblem(p: lb.Problem, psi: np.ndarray, g: np.ndarray, r: float,
                     eta: float = 0.1, eps_sub: float = 1e-13, max_iter: int = 20000,
-                    d0: np.ndarray | None = None, record: bool = False):
+                    d0: np.ndarray | None = None, record: bool = False, rel_tol: float = 0.0):
     """Algorithm 3 (adaptive implicit-explicit iteration) of the paper, in FP64.
 
     psi: the current iterate (physical field); g: the projected gradient there;
     r: trust-region radius; d0: initial point (default -r g / ||g||).
+    The stop test is the paper's ||g + (H + lambda I) d|| < eps_sub; with rel_tol > 0 the
+    iteration also stops once that residual is below rel_tol ||g|| (the relative form of
+    the test, which the paper's absolute eps_sub leaves open; default off).
     Returns a dict with d, lambda, iterations, final residual and (if record)
     per-iteration histories of lambda_k, ||d_k||, f(d_k) and the residual.
     """
@@ -98,6 +101,7 @@ def imex_subproblem(p: lb.Problem, psi: np.ndarray, g: np.ndarray, r: float,
     else:
         d = lb.project(np.asarray(d0, np.float64))
     hist = {"lambda": [], "dnorm": [], "f": [], "res": [], "newton": []}
+    tol = max(eps_sub, rel_tol * lb.norm(g))
     lam = 0.0
     res = np.inf
     it = 0
@@ -119,10 +123,10 @@ def imex_subproblem(p: lb.Problem, psi: np.ndarray, g: np.ndarray, r: float,
             hist["f"].append(model_value(p, psi, g, d))
             hist["res"].append(res)
             hist["newton"].append(nsteps)
-        if res < eps_sub:
+        if res < tol:
             break
     out = {"d": d, "lambda": lam, "iterations": it, "residual": res,
-           "converged": bool(res < eps_sub)}
+           "converged": bool(res < tol)}
     if record:
         out["history"] = hist
     return out

@@ -126,7 +126,7 @@ def contract(p: lb.Problem, v, g, r, mu, s_j, lam_j, prm, log=None):
 def imex_tr(p: lb.Problem, v0: np.ndarray, params: dict | None = None, max_outer: int = 500,
             eps: float | None = None, second_order: bool = True, tol2: float = 1e-8,
             max_inner: int = 20000, eps_sub: float | None = None, seed: int = 0,
-            log: list | None = None):
+            log: list | None = None, sub_rel_tol: float = 0.0):
     """Algorithm 1 of the paper with the readings listed in the module docstring.
 
     Returns a dict with the final field, energy, ||g||_inf, lambda_min (if checked),
@@ -163,7 +163,7 @@ def imex_tr(p: lb.Problem, v0: np.ndarray, params: dict | None = None, max_outer
                 status = "converged"
                 break
             d0 = random_ball_point(rng, p.shape, r)
-        sub = imex_subproblem(p, v, g, r, prm["eta"], prm["eps_sub"], max_inner, d0=d0)
+        sub = imex_subproblem(p, v, g, r, prm["eta"], prm["eps_sub"], max_inner, d0=d0, rel_tol=sub_rel_tol)
         d0 = None
         inner_total += sub["iterations"]
         s, lam_j = sub["d"], sub["lambda"]

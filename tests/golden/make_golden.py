@@ -30,7 +30,23 @@ def case_2d_64_plain():
     return w, dict(eps=1e-8, max_outer=200, max_inner=20000)
 
 
-CASES = {"2d_16_nonconvex": case_2d_16, "2d_64_plain": case_2d_64_plain}
+def case_3d_64_bcc_rel():
+    # 3D LB, 64^3, box 4 pi sqrt(2), tau = -0.1, gamma = 0.2, the BCC {110} start + noise:
+    # to ||g||_inf < 1e-8 and lambda_min >= -1e-8, inner iterations to a residual below
+    # 1e-4 ||g|| (at most 2000), the settings both GPU precisions are run with
+    w = inputs.config_3d_bcc(64)
+    return w, dict(eps=1e-8, max_outer=200, max_inner=2000, eps_sub=0.0, sub_rel_tol=1e-4)
+
+
+def case_3d_64_bcc_abs():
+    # the same problem with the paper's absolute inner test (eps_sub 1e-10, at most 5000
+    # inner iterations), a different path that ends at another SP-II of the same problem
+    w = inputs.config_3d_bcc(64)
+    return w, dict(eps=1e-8, max_outer=200, max_inner=5000, eps_sub=1e-10)
+
+
+CASES = {"2d_16_nonconvex": case_2d_16, "2d_64_plain": case_2d_64_plain,
+         "3d_64_bcc_rel": case_3d_64_bcc_rel, "3d_64_bcc_abs": case_3d_64_bcc_abs}
 
 
 def run(name):
@@ -41,7 +57,8 @@ def run(name):
     out = tr.imex_tr(p, w.phi0, log=log, **kw)
     lam = out["lambda_min"]
     if lam is None:
-        lam = eig.lanczos_lambda_min(p, out["v"], k_max=300, tol=1e-8)["theta"]
+        lam = eig.lanczos_lambda_min(p, out["v"], k_max=300, tol=1e-8)["theta"] if p.n > 1024 else \
+            float(eig.dense_eigs(p, out["v"], count=1)[0][0])
     return {"workload": w.name, "energy": out["E"], "gmax": out["gmax"], "lambda_min": lam,
             "status": out["status"], "outer": out["outer"], "inner": out["inner"],
             "oracle_seconds": time.time() - t0, "params": kw}
@@ -54,7 +71,14 @@ if __name__ == "__main__":
         with open(OUT) as f:
             data = json.load(f)
     for n in names:
-        data[n] = run(n)
-        with open(OUT, "w") as f:
+        res = run(n)
+        # re-read before writing: several cases may run as separate processes
+        if os.path.exists(OUT):
+            with open(OUT) as f:
+                data = json.load(f)
+        data[n] = res
+        tmp = OUT + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, OUT)
         print(n, data[n], flush=True)
