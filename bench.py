@@ -323,7 +323,10 @@ def time_tr(lbtr, w, prec: str, outer: int) -> dict:
     n_out = max(1, info["outer"])
     out = {"outer_iters": n_out, "seconds": dt, "tr_iters_per_s": n_out / dt,
            "inner_iters": info["inner"], "inner_iters_per_s": info["inner"] / dt,
-           "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6}
+           "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6,
+           "sub_stalled": info["sub_stalled"], "sub_capped": info["sub_capped"],
+           "sub_worst_rel_res": info["sub_worst_rel_res"],
+           "note": "outer iterations from the initial field, not a solve"}
     # per-kernel-class breakdown of one more outer iteration (CUDA events per launch)
     phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
     o.max_outer = 1
@@ -334,6 +337,46 @@ def time_tr(lbtr, w, prec: str, outer: int) -> dict:
     n1 = max(1, info1["inner"])
     out["profiled_outer_iteration"] = {"inner_iters": n1, "classes": {
         k: {"total_ms": v[0], "launches": v[1], "us_per_inner_iter": 1e3 * v[0] / n1} for k, v in prof.items() if v[1] > 0}}
+    return out
+
+
+def time_tr_solve_bcc64(lbtr, prec: str) -> dict:
+    """A whole IMEX-TR solve of the 3D BCC workload (64^3, box 4 pi sqrt(2), tau -0.1,
+    gamma 0.2) to max|g| < 1e-8 with the second-order test lambda_min >= -1e-8, inner
+    iterations to a residual below 1e-4 ||g|| (at most 2000): the same accuracy in both
+    precisions.  The oracle's solve with the same settings, when stored, gives the energy
+    the result is compared with."""
+    import torch
+    from paper_2603_03933_gb300 import inputs
+    w = inputs.config_3d_bcc(64)
+    ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
+                                        lbtr.LB_MIXED if prec == "mixed" else lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    o.eps, o.tol2, o.second_order = 1e-8, 1e-8, 1
+    o.sub.eps_sub, o.sub.rel_tol, o.sub.max_iter, o.sub.check_every = 0.0, 1e-4, 2000, 256
+    o.max_outer = 1                                       # warm-up
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
+    lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    o.max_outer = 200
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"status": info["status"], "seconds_to_solution": dt, "outer_iters": info["outer"],
+           "tr_iters_per_s": info["outer"] / dt, "inner_iters": info["inner"],
+           "inner_per_outer": info["inner"] / max(1, info["outer"]),
+           "energy": info["energy"], "gmax": info["gmax"], "lambda_min": info["lambda_min"],
+           "sub_stalled": info["sub_stalled"], "sub_capped": info["sub_capped"],
+           "sub_worst_rel_res": info["sub_worst_rel_res"]}
+    gold = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+    if os.path.exists(gold):
+        with open(gold) as f:
+            ref = json.load(f).get("3d_64_bcc_rel")
+        if ref:
+            out["oracle_energy"] = ref["energy"]
+            out["energy_minus_oracle"] = info["energy"] - ref["energy"]
     return out
 
 
@@ -421,6 +464,7 @@ def main():
                     help="instances of the batched 2D sweep timed as one CUDA graph (0: skip)")
     ap.add_argument("--sweep-solve-instances", type=int, default=16,
                     help="instances of the sweep solved whole by lb_batch_tr_solve (0: skip)")
+    ap.add_argument("--no-solve", action="store_true", help="skip the whole 64^3 BCC solves")
     ap.add_argument("--profile-sub", type=int, default=0,
                     help="profile this many IMEX inner iterations per precision and exit")
     args = ap.parse_args()
@@ -596,6 +640,17 @@ def main():
     if args.tr_outer > 0:
         for prec in ("mixed", "fp64"):
             tr[prec] = time_tr(lbtr, w, prec, args.tr_outer if prec == "mixed" else max(1, args.tr_outer // 2))
+    tr_solve = None
+    if not args.no_solve:
+        try:
+            tr_solve = {"workload": "3D BCC 64^3 (tau -0.1, gamma 0.2), to max|g| < 1e-8 and lambda_min >= -1e-8, "
+                                    "inner residual < 1e-4 ||g|| (<= 2000 iterations), both precisions"}
+            for prec in ("mixed", "fp64"):
+                tr_solve[prec] = time_tr_solve_bcc64(lbtr, prec)
+            tr_solve["time_ratio_fp64_over_mixed"] = (tr_solve["fp64"]["seconds_to_solution"] /
+                                                      tr_solve["mixed"]["seconds_to_solution"])
+        except Exception as ex:  # report, do not hide
+            tr_solve = {"error": str(ex)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -622,7 +677,7 @@ def main():
                    "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_hvp * args.batch * args.steps,
-        "fp64": fp64, "size_256": big, "tr": tr, "sweep": sweep, "sweep_solve": sweep_solve,
+        "fp64": fp64, "size_256": big, "tr": tr, "tr_solve": tr_solve, "sweep": sweep, "sweep_solve": sweep_solve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -220,3 +220,101 @@ def test_tr_resume_refuses_a_checkpoint_of_another_grid(lbtr, tmp_path):
     with pytest.raises(lbtr.LBError) as e:
         lbtr.lb_imex_tr_solve(ctx, phi, opts=o)
     assert e.value.status == 1
+
+
+def test_tr_resume_refuses_a_checkpoint_of_another_problem(lbtr, tmp_path):
+    # a checkpoint written for tau = -0.2 is not resumed by a context built for tau = -0.1
+    # on the same grid and box
+    w = inputs.random_problem((16, 16), 5, sigma=0.05, tau=-0.2, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    path = str(tmp_path / "tr").encode()
+    o.eps, o.checkpoint_path, o.checkpoint_every, o.max_outer = 1e-8, path, 1, 2
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    other = inputs.random_problem((16, 16), 5, sigma=0.05, tau=-0.1, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    ctx2 = _ctx(lbtr, other, lbtr.LB_FP64)
+    o.resume, o.max_outer = 1, 200
+    with pytest.raises(lbtr.LBError) as e:
+        lbtr.lb_imex_tr_solve(ctx2, torch.zeros_like(phi), opts=o)
+    assert e.value.status == 1 and "tau" in str(e.value)
+    # the matching context resumes
+    info = lbtr.lb_imex_tr_solve(ctx, torch.zeros_like(phi), opts=o)
+    assert info["status"] == 0
+
+
+def _trace_lines(err_text):
+    out = []
+    for line in err_text.splitlines():
+        line = line.strip()
+        if line.startswith("{\"j\""):
+            out.append(json.loads(line))
+    return out
+
+
+@pytest.mark.parametrize("params,steps", [(dict(r0=5.0, nu0=5.0), ["contract", "accept"]),
+                                          (dict(r0=0.01, mu0=1e4), ["shrink", "accept"]),
+                                          (dict(r0=0.01, nu0=0.01), ["accept", "accept"])])
+def test_tr_trajectory_matches_oracle_branch_by_branch(lbtr, capfd, monkeypatch, params, steps):
+    # Algorithm 1's first two outer iterations on an 8x8 problem, GPU (FP64, per-iteration
+    # trace) against the oracle: the same branch each time, and r, nu, mu, lambda, ||s||, rho
+    # of every iteration (inner solves to 1e-12, CONTRACT solves to 1e-10 relative)
+    from oracle import trust_region as otr
+    w = inputs.random_problem((8, 8), 11, sigma=0.3, tau=-0.2, gamma=0.3, box=(2 * math.pi, 2 * math.pi))
+    p = olb.Problem.from_workload(w)
+    log = []
+    otr.imex_tr(p, w.phi0, params=params, max_outer=2, eps=1e-12, second_order=False, max_inner=20000,
+                eps_sub=1e-12, log=log)
+    assert [e["step"] for e in log] == steps
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64)
+    o = lbtr.default_tr_opts()
+    for k, v in params.items():
+        setattr(o, k, v)
+    o.eps, o.max_outer, o.second_order = 1e-12, 2, 0
+    o.sub.eps_sub, o.sub.max_iter = 1e-12, 20000
+    monkeypatch.setenv("LBTR_TRACE", "1")
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    capfd.readouterr()
+    lbtr.lb_imex_tr_solve(ctx, phi, opts=o, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    tr = _trace_lines(capfd.readouterr().err)
+    assert len(tr) == 2
+    prev = (0, 0, 0)
+    for e, g in zip(log, tr):
+        cnt = (g["acc"], g["con"], g["shr"])
+        kind = ["accept", "contract", "shrink"][[c - q for c, q in zip(cnt, prev)].index(1)]
+        prev = cnt
+        assert kind == e["step"]
+        for key, gk in (("r", "r"), ("nu", "nu"), ("mu", "mu"), ("lambda", "lambda"), ("snorm", "snorm"),
+                        ("rho", "rho")):
+            # the trace prints 6 significant digits
+            assert abs(g[gk] - e[key]) <= 1e-5 * max(abs(e[key]), 1e-12) + 1e-12, (key, g[gk], e[key])
+
+
+def _c2_opts(lbtr, case):
+    o = lbtr.default_tr_opts()
+    o.eps, o.tol2, o.max_outer, o.second_order = 1e-8, 1e-8, 200, 1
+    if case == "3d_64_bcc_rel":
+        o.sub.eps_sub, o.sub.rel_tol, o.sub.max_iter = 0.0, 1e-4, 2000
+    else:
+        o.sub.eps_sub, o.sub.rel_tol, o.sub.max_iter = 1e-10, 0.0, 5000
+    return o
+
+
+@pytest.mark.parametrize("case,prec", [("3d_64_bcc_rel", "fp64"), ("3d_64_bcc_rel", "mixed"),
+                                       ("3d_64_bcc_abs", "fp64")])
+def test_tr_solve_3d_64_bcc_matches_oracle(lbtr, case, prec):
+    # the 64^3 BCC workload solved to ||g||_inf < 1e-8 with the second-order test, with the
+    # inner settings of the oracle's own solve: the energy within 1e-8 of the oracle's and the
+    # same sign of lambda_min (|lambda_min| <= 1e-8 counts as >= 0)
+    ref = _golden(case)
+    w = inputs.config_3d_bcc(64)
+    p = olb.Problem.from_workload(w)
+    ctx = _ctx(lbtr, w, lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED)
+    phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
+    info = lbtr.lb_imex_tr_solve(ctx, phi, opts=_c2_opts(lbtr, case))
+    v = phi.cpu().numpy()
+    assert np.max(np.abs(olb.gradient(p, v))) < 1e-8
+    assert abs(info["energy"] - olb.energy(p, v)) < 1e-12
+    assert abs(info["energy"] - ref["energy"]) < 1e-8
+    assert (info["lambda_min"] >= -1e-8) == (ref["lambda_min"] >= -1e-8)
