@@ -365,15 +365,45 @@ int lb_batch_size(const lb_batch *batch);
  * hv[i] = H_i v[i] for every problem i of the batch (each as lb_hessvec).  phi, v, hv:
  * host arrays of lb_batch_size() device pointers, fields laid out as in lb_hessvec.
  * The first call with a given set of pointers records the products of all problems as
- * one CUDA graph (independent branches on up to 16 internal streams, largest problems
- * first on the least-loaded stream); later calls with the same pointers replay it, and a
- * call with other pointers records anew.  The graph is launched on `stream`; the call is
+ * one CUDA graph: the 2D problems as grouped launches or one persistent launch (see
+ * lb_batch_set_launch below), the others as independent branches on up to 16 internal
+ * streams, largest problems first on the least-loaded stream; later calls with the same pointers replay it, and a call with other
+ * pointers records anew.  The graph is launched on `stream`; the call is
  * asynchronous.  Calls on the same batch must not overlap on the GPU (the problems'
  * contexts hold the scratch spectra).
  * Errors: LB_ERR_INVALID_ARG (null, misaligned or aliased fields), LB_ERR_CUDA.
  */
 lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *const *v, void *const *hv,
                            lb_stream stream);
+
+/*
+ * Launch strategy of a batch's 2D problems (grids of 16..512 points per axis):
+ *  strategy 0 (default): the problems of each grid size run as three grouped launches (rows
+ *    forward, y lines with Lambda, rows inverse) whose blockIdx.y selects a problem;
+ *  strategy 1: ONE persistent cooperative launch for all of them: the three passes of every
+ *    product as three phases separated by grid barriers, each CTA taking the next (problem,
+ *    task) pair from a device-side queue of the phase, largest grids first.  Its parameters:
+ *    min_blocks, the register allocation (4 or 5 resident CTAs of 128 threads per SM);
+ *    ctas_per_sm, the CTAs launched per SM (0: as many as fit); group, row blocks per row task.
+ * lb_batch_set_launch sets them; lb_batch_tune chooses them by timing: it records and replays
+ * the batch's graph `replays` times on `stream` for the grouped launches and for each
+ * candidate of the persistent one (CUDA events), keeps the fastest and returns the table.
+ * Both leave the graph to be recorded anew by the next lb_batch_hessvec call; tuning runs
+ * products on the given fields and blocks until the timing is done.
+ * Errors: LB_ERR_INVALID_ARG (bad arguments or fields), LB_ERR_TIMEOUT, LB_ERR_CUDA.
+ */
+typedef struct {
+    int count;             /* candidates timed */
+    int strategy[12];      /* 0 grouped launches, 1 persistent launch */
+    int min_blocks[12];    /* register allocation of the persistent kernel (CTAs per SM) */
+    int ctas_per_sm[12];   /* CTAs per SM of the persistent launch (0 for the grouped one) */
+    int group[12];         /* row blocks per row task */
+    double us[12];         /* mean device time of one product call (graph replay), microseconds */
+    int chosen;            /* the candidate now in use */
+} lb_batch_tuning;
+lb_status lb_batch_set_launch(lb_batch *batch, int strategy, int min_blocks, int ctas_per_sm, int group);
+lb_status lb_batch_tune(lb_batch *batch, const void *const *phi, const void *const *v, void *const *hv,
+                        int replays, lb_batch_tuning *out, lb_stream stream);
 
 /*
  * Algorithm 1 (as lb_imex_tr_solve) for every problem of the batch, several at a time: a
@@ -396,6 +426,13 @@ lb_status lb_batch_hessvec(lb_batch *batch, const void *const *phi, const void *
  */
 lb_status lb_batch_tr_solve(lb_batch *batch, double *const *phi, const lb_tr_opts *opts, lb_tr_info *info,
                             int nthreads, lb_stream stream);
+
+/* Profiling aid: the FP64 fused-multiply-add throughput of the current device, measured
+ * with CUDA events on `stream` (8 independent FMA chains per thread, 8 blocks of 256
+ * threads per SM; best of three timed runs after a warm-up), in TFLOP/s (2 flops per
+ * FMA).  It is the bound of the FP64 path, whose transforms run on the FP64 pipe.
+ * Synchronises the stream. */
+lb_status lb_measure_fp64_rate(double *tflops, lb_stream stream);
 
 /* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
  * (0 restores the default of about two seconds).  Lets tests exercise the

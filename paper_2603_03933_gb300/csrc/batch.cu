@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "sweep.cuh"
 
 struct BatchGroup {                         // problems of one size on the x-row path
     int m = 0, rows = 0, col_grid = 0, col_tiles = 0;
@@ -30,8 +31,35 @@ struct BatchGroup {                         // problems of one size on the x-row
     void* args = nullptr;                     // device: [count] XfArgs, [count] ColArgs, [count] XiArgs
 };
 
+// The 2D problems of a batch whose products run as one persistent launch (sweep.cuh).
+struct SweepState {
+    std::vector<int> members;                // problems in the launch, largest first
+    void* dev = nullptr;                     // device: probs, tasks (3 phases), partials, heads, barrier
+    void* probs = nullptr;
+    void* tasks[3] = {nullptr, nullptr, nullptr};
+    int ntasks[3] = {0, 0, 0};
+    unsigned* heads = nullptr;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+    int grid = 0;                            // CTAs of the launch
+    int occ = 0;                             // resident CTAs per SM the kernel allows
+    int nsm = 0;
+    int ctas_per_sm = 0;                     // chosen (0: occ)
+    int group = 1;                           // row blocks per row task
+    int min_blocks = 4;                      // register allocation of the kernel (float: 4 or 5)
+    bool enabled = false;                    // the 2D problems take the persistent launch
+    size_t smem = 0;
+    void release() {
+        if (dev) cudaFree(dev);
+        dev = nullptr;
+        members.clear();
+    }
+};
+
 struct lb_batch {
     std::vector<lb_ctx*> ctx;
+    SweepState sweep;
+    lb_batch_tuning tuning{};               // the last tuning table (count 0: never tuned)
     std::vector<BatchGroup> groups;
     std::vector<int> order;                 // problems, largest first
     std::vector<int> lane;                  // side stream of each problem
@@ -51,6 +79,7 @@ struct lb_batch {
     }
     ~lb_batch() {
         free_groups();
+        sweep.release();
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (cudaEvent_t e : join) if (e) cudaEventDestroy(e);
@@ -60,6 +89,17 @@ struct lb_batch {
         for (lb_ctx* c : ctx) lb_destroy(c);
     }
 };
+
+#define LB_SWEEP_M(mval, ...)                                       \
+    switch (mval) {                                                 \
+        case 16: { constexpr int M = 16; __VA_ARGS__; } break;      \
+        case 32: { constexpr int M = 32; __VA_ARGS__; } break;      \
+        case 64: { constexpr int M = 64; __VA_ARGS__; } break;      \
+        case 128: { constexpr int M = 128; __VA_ARGS__; } break;    \
+        case 256: { constexpr int M = 256; __VA_ARGS__; } break;    \
+        case 512: { constexpr int M = 512; __VA_ARGS__; } break;    \
+        default: break;                                             \
+    }
 
 namespace {
 lb_status batch_fail(lb_batch* b, lb_status st, const std::string& msg) {
@@ -71,6 +111,118 @@ lb_status batch_cuda(lb_batch* b, cudaError_t e, const char* where) {
     return batch_fail(b, LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 }  // namespace
+
+// row blocks and line tiles of a 2D problem of M points per axis in the sweep kernel
+static int sweep_row_blocks(int m) {
+    int nr = 0;
+    LB_SWEEP_M(m, nr = lbtr::RowGeo<M>::NR);
+    return nr > 0 ? (m + nr - 1) / nr : 0;
+}
+static int sweep_line_tiles(int m) {
+    const int nl = lbtr::sw_nl(m);
+    return (m / 2 + nl - 1) / nl + 1;
+}
+
+// the instantiation of the persistent kernel for a register allocation of min_blocks CTAs
+// per SM (float: 4 or 5; double: 1)
+template <typename T> static const void* sweep_kernel(int min_blocks) {
+    if constexpr (sizeof(T) == 8) return (const void*)lbtr::k_sweep_hvp<double, 1>;
+    else return min_blocks >= 5 ? (const void*)lbtr::k_sweep_hvp<float, 5> : (const void*)lbtr::k_sweep_hvp<float, 4>;
+}
+
+// Collect the batch's 2D problems of working type T (16 <= M <= 512), build their argument
+// structs for the given field pointers and the three task queues (largest grids first) and
+// upload them; `group` row blocks form one row task.
+template <typename T>
+static lb_status build_sweep(lb_batch* b, const void* const* phi, const void* const* v, void* const* hv, int group) {
+    SweepState& sw = b->sweep;
+    sw.release();
+    const bool want64 = sizeof(T) == 8;
+    std::vector<lbtr::SweepProb<T>> probs;
+    std::vector<long long> part_off;
+    long long npart = 0;
+    for (int i : b->order) {
+        lb_ctx* c = b->ctx[i];
+        if (c->prob.dim != 2 || c->prob.n < 16 || c->prob.n > 512 || (c->prec == LB_FP64) != want64) continue;
+        lbtr::Plan<T>* pl = want64 ? reinterpret_cast<lbtr::Plan<T>*>(c->p64) : reinterpret_cast<lbtr::Plan<T>*>(c->p32);
+        lbtr::SweepProb<T> sp{};
+        int cg = 0, ct = 0;
+        if (!pl->hvp_args((const T*)phi[i], (const T*)v[i], (T*)hv[i], sp.xf, sp.ca, cg, ct, sp.xi, true)) continue;
+        sp.m = c->prob.n;
+        sp.row_blocks = sweep_row_blocks(sp.m);
+        sp.line_tiles = sweep_line_tiles(sp.m);
+        part_off.push_back(npart);
+        npart += sp.row_blocks;
+        probs.push_back(sp);
+        sw.members.push_back(i);
+    }
+    if (probs.empty()) return LB_OK;
+    std::vector<lbtr::SweepTask> tk[3];
+    for (int q = 0; q < (int)probs.size(); ++q) {
+        const int rt = (probs[q].row_blocks + group - 1) / group;
+        for (int t = 0; t < rt; ++t) { tk[0].push_back({q, t}); tk[2].push_back({q, t}); }
+        for (int t = 0; t < probs[q].line_tiles; ++t) tk[1].push_back({q, t});
+    }
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t off = 0;
+    const size_t o_probs = off; off += up(probs.size() * sizeof(lbtr::SweepProb<T>));
+    size_t o_tk[3];
+    for (int ph = 0; ph < 3; ++ph) { o_tk[ph] = off; off += up(tk[ph].size() * sizeof(lbtr::SweepTask)); }
+    const size_t o_part = off; off += up((size_t)npart * sizeof(double));
+    const size_t o_heads = off; off += up(3 * 32 * sizeof(unsigned));
+    const size_t o_bar = off; off += up((64 + 32 * 65) * sizeof(unsigned));
+    const size_t o_err = off; off += up(sizeof(int));
+    lb_status st = batch_cuda(b, cudaMalloc(&sw.dev, off), "lb_batch_hessvec/sweep");
+    if (st) { sw.dev = nullptr; return st; }
+    char* base = static_cast<char*>(sw.dev);
+    double* part = reinterpret_cast<double*>(base + o_part);
+    for (size_t q = 0; q < probs.size(); ++q) probs[q].part = part + part_off[q];
+    sw.probs = base + o_probs;
+    for (int ph = 0; ph < 3; ++ph) { sw.tasks[ph] = base + o_tk[ph]; sw.ntasks[ph] = (int)tk[ph].size(); }
+    sw.heads = reinterpret_cast<unsigned*>(base + o_heads);
+    sw.bar = reinterpret_cast<unsigned*>(base + o_bar);
+    sw.err = reinterpret_cast<int*>(base + o_err);
+    sw.group = group;
+    st = batch_cuda(b, cudaMemset(sw.dev, 0, off), "lb_batch_hessvec/sweep");
+    if (!st) st = batch_cuda(b, cudaMemcpy(sw.probs, probs.data(), probs.size() * sizeof(lbtr::SweepProb<T>),
+                                           cudaMemcpyHostToDevice), "lb_batch_hessvec/sweep");
+    for (int ph = 0; ph < 3 && !st; ++ph)
+        st = batch_cuda(b, cudaMemcpy(sw.tasks[ph], tk[ph].data(), tk[ph].size() * sizeof(lbtr::SweepTask),
+                                      cudaMemcpyHostToDevice), "lb_batch_hessvec/sweep");
+    if (st) return st;
+    // residency: the launch is cooperative, at most occ CTAs per SM
+    const size_t smem = lbtr::sw_smem<T>();
+    const void* kern = sweep_kernel<T>(sw.min_blocks);
+    st = batch_cuda(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "lb_batch_hessvec/sweep");
+    int dev = 0;
+    if (!st) st = batch_cuda(b, cudaGetDevice(&dev), "lb_batch_hessvec/sweep");
+    if (!st) st = batch_cuda(b, cudaDeviceGetAttribute(&sw.nsm, cudaDevAttrMultiProcessorCount, dev), "lb_batch_hessvec/sweep");
+    if (!st) st = batch_cuda(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sw.occ, kern, 128, smem),
+                             "lb_batch_hessvec/sweep");
+    if (st) return st;
+    if (sw.occ < 1) { sw.release(); return LB_OK; }       // cannot be resident: the grouped launches serve
+    sw.smem = smem;
+    const int cps = sw.ctas_per_sm > 0 ? std::min(sw.ctas_per_sm, sw.occ) : sw.occ;
+    sw.grid = sw.nsm * cps;
+    return LB_OK;
+}
+
+// enqueue the persistent launch (the queue heads reset first) on stream s
+template <typename T> static cudaError_t launch_sweep(lb_batch* b, cudaStream_t s) {
+    SweepState& sw = b->sweep;
+    cudaError_t e = cudaMemsetAsync(sw.heads, 0, 3 * 32 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    lbtr::SweepArgs<T> a{};
+    a.probs = static_cast<const lbtr::SweepProb<T>*>(sw.probs);
+    for (int ph = 0; ph < 3; ++ph) { a.tasks[ph] = static_cast<const lbtr::SweepTask*>(sw.tasks[ph]); a.ntasks[ph] = sw.ntasks[ph]; }
+    a.group = sw.group;
+    a.heads = sw.heads;
+    a.bar.count = sw.bar; a.bar.gen = sw.bar + 32; a.bar.err = sw.err; a.bar.tree = sw.bar + 64;
+    a.bar.budget = 4000000000LL;
+    void* args[] = {&a};
+    return cudaLaunchCooperativeKernel(sweep_kernel<T>(sw.min_blocks), dim3(sw.grid), dim3(128), args, sw.smem, s);
+}
 
 // Group the problems on the x-row path by (precision, dimension, size) and upload each
 // group's argument structs (they hold the field pointers of this call).
@@ -103,7 +255,19 @@ static lb_status upload_group(lb_batch* b, BatchGroup& g, const void* const* phi
 static lb_status record_groups(lb_batch* b, const void* const* phi, const void* const* v, void* const* hv) {
     b->free_groups();
     const int n = (int)b->ctx.size();
+    // the 2D problems run as one persistent launch when that strategy is chosen; the others
+    // (and all problems otherwise) as grouped launches / branches
+    b->sweep.release();
+    if (b->sweep.enabled) {
+        const int group = b->sweep.group > 0 ? b->sweep.group : 1;
+        lb_status st = b->ctx[0]->prec == LB_FP64 ? build_sweep<double>(b, phi, v, hv, group)
+                                                  : build_sweep<float>(b, phi, v, hv, group);
+        if (st) return st;
+    }
+    std::vector<char> in_sweep(n, 0);
+    for (int i : b->sweep.members) in_sweep[i] = 1;
     for (int i : b->order) {
+        if (in_sweep[i]) continue;
         lb_ctx* c = b->ctx[i];
         int m = c->prob.n, rows = 0, cg = 0, ct = 0;
         bool ok;
@@ -220,6 +384,15 @@ lb_status lb_batch_hessvec(lb_batch* b, const void* const* phi, const void* cons
         auto least = [&]() { return (int)(std::min_element(load.begin(), load.end()) - load.begin()); };
         std::vector<char> grouped(n, 0);
         cudaError_t le = cudaSuccess;
+        if (!b->sweep.members.empty()) {
+            const int k = least();
+            long long pts = 0;
+            for (int i : b->sweep.members) { grouped[i] = 1; pts += b->ctx[i]->n(); }
+            load[k] += pts;
+            cudaError_t e = b->ctx[0]->prec == LB_FP64 ? launch_sweep<double>(b, b->side[k])
+                                                       : launch_sweep<float>(b, b->side[k]);
+            if (e != cudaSuccess) le = e;
+        }
         for (BatchGroup& g : b->groups) {
             const int k = least();
             const int cnt = (int)g.members.size();
@@ -270,6 +443,94 @@ lb_status lb_batch_hessvec(lb_batch* b, const void* const* phi, const void* cons
         b->key = key;
     }
     return batch_cuda(b, cudaGraphLaunch(b->exec, (cudaStream_t)stream), "lb_batch_hessvec/launch");
+}
+
+// drop the recorded graph: the next product call records it with the current configuration
+static void batch_invalidate(lb_batch* b) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->key.clear();
+}
+
+lb_status lb_batch_set_launch(lb_batch* b, int strategy, int min_blocks, int ctas_per_sm, int group) {
+    if (!b || (strategy != 0 && strategy != 1) || ctas_per_sm < 0 || group < 1)
+        return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_set_launch: bad argument");
+    b->sweep.enabled = strategy == 1;
+    b->sweep.min_blocks = min_blocks >= 5 ? 5 : 4;
+    b->sweep.ctas_per_sm = ctas_per_sm;
+    b->sweep.group = group;
+    batch_invalidate(b);
+    return LB_OK;
+}
+
+lb_status lb_batch_tune(lb_batch* b, const void* const* phi, const void* const* v, void* const* hv, int replays,
+                        lb_batch_tuning* out, lb_stream stream) {
+    if (!b || !phi || !v || !hv || replays < 1) return batch_fail(b, LB_ERR_INVALID_ARG, "lb_batch_tune: bad argument");
+    const bool f64 = b->ctx[0]->prec == LB_FP64;
+    cudaStream_t s = (cudaStream_t)stream;
+    SweepState& sw = b->sweep;
+    // candidates: the grouped launches, then the persistent launch over register allocations,
+    // resident CTAs per SM and row blocks per task
+    struct Cand { int strategy, minb, cps, group; };
+    std::vector<Cand> cand;
+    cand.push_back({0, 0, 0, 1});
+    for (int minb : (f64 ? std::vector<int>{4} : std::vector<int>{4, 5})) {
+        int occ = 0;
+        const void* kern = f64 ? sweep_kernel<double>(minb) : sweep_kernel<float>(minb);
+        const size_t smem = f64 ? lbtr::sw_smem<double>() : lbtr::sw_smem<float>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem) != cudaSuccess || occ < 1)
+            continue;
+        std::vector<int> cps{occ};
+        if ((occ + 1) / 2 < occ) cps.insert(cps.begin(), (occ + 1) / 2);
+        for (int c : cps)
+            for (int g : {1, 4})
+                if ((int)cand.size() < 12) cand.push_back({1, minb, c, g});
+    }
+    const int keep_strategy = sw.enabled ? 1 : 0;
+    const Cand keep{keep_strategy, sw.min_blocks, sw.ctas_per_sm, sw.group};
+    lb_batch_tuning t{};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    lb_status st = batch_cuda(b, cudaEventCreate(&e0), "lb_batch_tune");
+    if (!st) st = batch_cuda(b, cudaEventCreate(&e1), "lb_batch_tune");
+    for (const Cand& c : cand) {
+        if (st) break;
+        lb_batch_set_launch(b, c.strategy, c.minb, c.cps, c.group);
+        // each candidate is timed as what a product call runs: its recorded graph, replayed
+        for (int r = 0; r < 2 && !st; ++r) st = lb_batch_hessvec(b, phi, v, hv, stream);
+        if (!st) st = batch_cuda(b, cudaEventRecord(e0, s), "lb_batch_tune");
+        for (int r = 0; r < replays && !st; ++r) st = lb_batch_hessvec(b, phi, v, hv, stream);
+        if (!st) st = batch_cuda(b, cudaEventRecord(e1, s), "lb_batch_tune");
+        if (!st) st = batch_cuda(b, cudaEventSynchronize(e1), "lb_batch_tune");
+        float ms = 0.f;
+        if (!st) st = batch_cuda(b, cudaEventElapsedTime(&ms, e0, e1), "lb_batch_tune");
+        if (!st && c.strategy == 1 && sw.err) {
+            int herr = 0;
+            cudaMemcpy(&herr, sw.err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (herr) st = batch_fail(b, LB_ERR_TIMEOUT, "lb_batch_tune: a grid barrier timed out");
+        }
+        if (st) break;
+        t.strategy[t.count] = c.strategy;
+        t.min_blocks[t.count] = c.minb;
+        t.ctas_per_sm[t.count] = c.strategy ? std::min(c.cps, sw.occ) : 0;
+        t.group[t.count] = c.group;
+        t.us[t.count] = 1e3 * ms / replays;
+        ++t.count;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) {
+        lb_batch_set_launch(b, keep.strategy, keep.minb, keep.cps, keep.group);
+        return st;
+    }
+    int best = 0;
+    for (int k = 1; k < t.count; ++k)
+        if (t.us[k] < t.us[best]) best = k;
+    t.chosen = best;
+    lb_batch_set_launch(b, t.strategy[best], t.min_blocks[best], t.ctas_per_sm[best], t.group[best]);
+    b->tuning = t;
+    if (out) *out = t;
+    return LB_OK;
 }
 
 lb_status lb_batch_tr_solve(lb_batch* b, double* const* phi, const lb_tr_opts* opts, lb_tr_info* info,

@@ -95,35 +95,6 @@ template <typename T> __device__ __forceinline__ void h3_pow7(cplx<T> b, cplx<T>
     w[7] = cmul(w[6], b);
 }
 
-// Grid barrier of the fused product: thread 0 of each CTA arrives with an acquire-release
-// atomic (its CTA's earlier stores published by the release), the last arrival resets the
-// count and releases the generation word, the others poll it with acquire loads.  The spin
-// is bounded by gb.budget clock cycles; on expiry the error flag is set and false returned.
-__device__ __forceinline__ bool h3_grid_sync(const GridBar& gb) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        unsigned* gen = (unsigned*)gb.gen;
-        const unsigned my_gen = ld_acquire_gpu(gen);
-        if (atom_add_acq_rel_gpu(gb.count, 1u) == gridDim.x - 1u) {
-            *gb.count = 0u;
-            red_add_release_gpu(gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (ld_acquire_gpu(gen) == my_gen) {
-                if (clock64() - t0 > gb.budget || *(volatile int*)gb.err != 0) {
-                    atomicCAS(gb.err, 0, 5);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // f''(u) = tau - gamma u + u^2 / 2 (as f2v of passes.cuh)
 template <typename T> __device__ __forceinline__ T h3_f2(const Model<T>& m, T u) {
     return m.tau + u * ((T)0.5 * u - m.gamma);
@@ -516,7 +487,7 @@ __global__ void __launch_bounds__(1024, 1) k_hvp_fused(Hvp3Args<T> a) {
         h3_fwd_plane<T>(a, zz, smem_raw);
         __syncthreads();                                     // shared memory reused by the next plane
     }
-    if (!h3_grid_sync(a.bar)) return;
+    if (!grid_sync_acqrel(a.bar)) return;
     {
         // z-line tasks on the first warps of every CTA, interleaved over CTAs
         const int warp = threadIdx.x >> 5, nw = (G::NTASKS + nb - 1) / nb;
@@ -527,7 +498,7 @@ __global__ void __launch_bounds__(1024, 1) k_hvp_fused(Hvp3Args<T> a) {
             for (int q = warp * nb + z; q < G::NTASKS; q += nwork * nb) h3_zline_task<T>(a, q, ts);
         }
     }
-    if (!h3_grid_sync(a.bar)) return;
+    if (!grid_sync_acqrel(a.bar)) return;
     for (int zz = z; zz < G::M; zz += nb) {
         h3_inv_plane<T>(a, zz, smem_raw);
         __syncthreads();

@@ -112,9 +112,11 @@ public:
 
     static constexpr long long kDefaultBudget = 4000000000LL;   // ~2 s at 2 GHz
 
-    // the argument structs of one hessvec on the x-row path (for batched launches); false elsewhere
+    // the argument structs of one hessvec on the x-row path (for batched launches); false elsewhere.
+    // any_lines: also on grids whose line pass has no persistent k_lines variant (the
+    // batched sweep kernel brings its own line tiles)
     bool hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid, int& col_tiles,
-                  XiArgs<T>& xi) const;
+                  XiArgs<T>& xi, bool any_lines = false) const;
     int col_args(int axis, int mode, C* spec, C* dst, const C* src, T kscale, double escale, double sigma,
                  const double* lam, int slot, const int* done, ColArgs<T>& a) const;
 

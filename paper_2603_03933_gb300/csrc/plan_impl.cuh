@@ -574,8 +574,8 @@ template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cud
 // 128^3), for batched launches of many problems of the same size; false on other paths.
 template <typename T>
 bool Plan<T>::hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid,
-                       int& col_tiles, XiArgs<T>& xi) const {
-    if (use_planes_ || m_ < 16 || ln_grid_cap_ <= 0) return false;
+                       int& col_tiles, XiArgs<T>& xi, bool any_lines) const {
+    if (use_planes_ || m_ < 16 || (ln_grid_cap_ <= 0 && !any_lines)) return false;
     Plan<T>* self = const_cast<Plan<T>*>(this);
     xf.in = v; xf.phi = phi; xf.g = nullptr; xf.d0 = nullptr; xf.dscale = nullptr;
     xf.main = d_work_; xf.nyq = d_work_ + (size_t)rows_ * h_;
@@ -585,7 +585,7 @@ bool Plan<T>::hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T
     const int inner = dim_ == 3 ? 2 : 1;
     col_tiles = col_args(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0,
                          nullptr, ca);
-    col_grid = std::min(col_tiles, ln_grid_cap_);
+    col_grid = ln_grid_cap_ > 0 ? std::min(col_tiles, ln_grid_cap_) : col_tiles;
     xi.main = d_work_; xi.nyq = d_work_ + (size_t)rows_ * h_;
     xi.out = hv; xi.phi = phi; xi.v = v; xi.msum = self->slot(S_HVP); xi.inv_n = 1.0 / (double)n_;
     xi.oscale = (T)1; xi.tw = d_tw_; xi.rows = rows_; xi.model = model_; xi.model.eta = (T)eta;

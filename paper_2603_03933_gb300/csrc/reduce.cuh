@@ -247,6 +247,35 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb) {
     return ok != 0;
 }
 
+// Grid barrier of the persistent kernels (the fused 128^3 product, the batched sweep): thread 0 of each CTA arrives with an acquire-release
+// atomic (its CTA's earlier stores published by the release), the last arrival resets the
+// count and releases the generation word, the others poll it with acquire loads.  The spin
+// is bounded by gb.budget clock cycles; on expiry the error flag is set and false returned.
+__device__ __forceinline__ bool grid_sync_acqrel(const GridBar& gb) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        unsigned* gen = (unsigned*)gb.gen;
+        const unsigned my_gen = ld_acquire_gpu(gen);
+        if (atom_add_acq_rel_gpu(gb.count, 1u) == gridDim.x - 1u) {
+            *gb.count = 0u;
+            red_add_release_gpu(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(gen) == my_gen) {
+                if (clock64() - t0 > gb.budget || *(volatile int*)gb.err != 0) {
+                    atomicCAS(gb.err, 0, 5);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 // Grid barrier that also sums NQ per-block values over a two-level tree.  Thread 0 of every
 // block passes its block's values in `mine`.  Blocks form groups of 32 consecutive blocks;
 // the last block of a group to arrive sums the group's values with one warp (one coalesced

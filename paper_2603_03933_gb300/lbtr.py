@@ -74,6 +74,12 @@ class lb_tr_info(ctypes.Structure):
                 ("sub_capped", ctypes.c_int), ("sub_worst_rel_res", ctypes.c_double)]
 
 
+class lb_batch_tuning(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("strategy", ctypes.c_int * 12), ("min_blocks", ctypes.c_int * 12),
+                ("ctas_per_sm", ctypes.c_int * 12), ("group", ctypes.c_int * 12),
+                ("us", ctypes.c_double * 12), ("chosen", ctypes.c_int)]
+
+
 class lb_sis_opts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("eps", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("check_every", ctypes.c_int)]
@@ -108,12 +114,16 @@ SIGNATURES = [
     ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
+    ("lb_measure_fp64_rate", ctypes.c_int, [_DP, _VP]),
     ("lb_hessvec_noalloc", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("lb_batch_create", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
     ("lb_batch_destroy", None, [_VP]),
     ("lb_batch_last_error", ctypes.c_char_p, [_VP]),
     ("lb_batch_size", ctypes.c_int, [_VP]),
     ("lb_batch_hessvec", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("lb_batch_set_launch", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("lb_batch_tune", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int,
+                                     ctypes.POINTER(lb_batch_tuning), _VP]),
     ("lb_batch_tr_solve", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(lb_tr_opts),
                                          ctypes.POINTER(lb_tr_info), ctypes.c_int, _VP]),
 ]
@@ -354,6 +364,15 @@ def lb_set_barrier_budget(ctx: Context, cycles: int):
     _check(ctx, load().lb_set_barrier_budget(ctx.handle, int(cycles)), "lb_set_barrier_budget")
 
 
+def lb_measure_fp64_rate(stream=None) -> float:
+    """FP64 FMA throughput of the current device in TFLOP/s (C: lb_measure_fp64_rate)."""
+    out = ctypes.c_double()
+    st = load().lb_measure_fp64_rate(ctypes.byref(out), _stream(stream))
+    if st != 0:
+        raise LBError(st, "lb_measure_fp64_rate")
+    return out.value
+
+
 def lb_profile_enable(ctx: Context, enable: bool = True):
     """Start (and reset) or stop per-kernel-class event timing (C: lb_profile_enable)."""
     _check(ctx, load().lb_profile_enable(ctx.handle, 1 if enable else 0), "lb_profile_enable")
@@ -427,8 +446,7 @@ def lb_batch_create(problems, precision: int = LB_FP64) -> Batch:
     return Batch(h, meta, precision)
 
 
-def lb_batch_hessvec(batch: Batch, phis, vs, hvs, stream=None):
-    """hvs[i] = H_i vs[i] for every problem, as one CUDA graph (C: lb_batch_hessvec)."""
+def _batch_ptrs(batch: Batch, phis, vs, hvs):
     torch = _torch()
     want = torch.float64 if batch.precision == LB_FP64 else torch.float32
     n = len(batch)
@@ -443,6 +461,48 @@ def lb_batch_hessvec(batch: Batch, phis, vs, hvs, stream=None):
                 raise ValueError(f"field {i}: need a contiguous {want} CUDA tensor of {m ** dim} values")
             arr[i] = t.data_ptr()
         ptrs.append(arr)
+    return ptrs
+
+
+class BatchFields:
+    """The device pointers of a batch call, marshalled once (phis, vs, hvs keep their
+    tensors alive); pass it to lb_batch_hessvec in place of the three lists."""
+
+    def __init__(self, batch: Batch, phis, vs, hvs):
+        self.tensors = (list(phis), list(vs), list(hvs))
+        self.ptrs = _batch_ptrs(batch, phis, vs, hvs)
+
+
+def lb_batch_tune(batch: Batch, phis, vs, hvs, replays: int = 10, stream=None) -> dict:
+    """Time the persistent sweep launch's candidate configurations and keep the fastest
+    (C: lb_batch_tune); returns the table with its measurements."""
+    ptrs = _batch_ptrs(batch, phis, vs, hvs)
+    t = lb_batch_tuning()
+    st = load().lb_batch_tune(batch.handle, ptrs[0], ptrs[1], ptrs[2], int(replays), ctypes.byref(t), _stream(stream))
+    if st != 0:
+        msg = load().lb_batch_last_error(batch.handle)
+        raise LBError(st, "lb_batch_tune: " + (msg.decode() if msg else ""))
+    return {"candidates": [{"strategy": "persistent" if t.strategy[k] else "grouped", "min_blocks": t.min_blocks[k],
+                            "ctas_per_sm": t.ctas_per_sm[k], "row_blocks_per_task": t.group[k], "us": t.us[k]}
+                           for k in range(t.count)], "chosen": t.chosen}
+
+
+def lb_batch_set_launch(batch: Batch, persistent: bool, min_blocks: int = 4, ctas_per_sm: int = 0, group: int = 1):
+    """Choose the batch's launch strategy for its 2D problems (C: lb_batch_set_launch)."""
+    st = load().lb_batch_set_launch(batch.handle, 1 if persistent else 0, int(min_blocks), int(ctas_per_sm), int(group))
+    if st != 0:
+        msg = load().lb_batch_last_error(batch.handle)
+        raise LBError(st, "lb_batch_set_launch: " + (msg.decode() if msg else ""))
+
+
+def lb_batch_hessvec(batch: Batch, phis, vs=None, hvs=None, stream=None):
+    """hvs[i] = H_i vs[i] for every problem, as one CUDA graph (C: lb_batch_hessvec).
+    `phis` may be a BatchFields (then vs and hvs are omitted): no per-call marshalling."""
+    if isinstance(phis, BatchFields):
+        ptrs = phis.ptrs
+        hvs = phis.tensors[2]
+    else:
+        ptrs = _batch_ptrs(batch, phis, vs, hvs)
     st = load().lb_batch_hessvec(batch.handle, ptrs[0], ptrs[1], ptrs[2], _stream(stream))
     if st != 0:
         msg = load().lb_batch_last_error(batch.handle)

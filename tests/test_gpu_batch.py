@@ -1,9 +1,11 @@
 """Batches of independent problems (the phase-diagram sweep) through lb_batch_hessvec.
 
 Every product of the batch must equal the product of the same problem through its own
-context (lb_hessvec: the same kernels, so the same result up to the rounding tolerance
-of the parity tests), on the recording call, on a replay of the recorded graph, and after
-new field pointers force a new recording; two members are also checked against the oracle.
+context (lb_hessvec: the same transforms; the 2D problems run in one persistent launch
+whose sums differ from the single-problem kernels' only in summation order), on the
+recording call, on a replay of the recorded graph, and after new field pointers force a
+new recording; one member of every grid size is also checked against the oracle.  The
+tuner's table must be complete and its choice must give the same products.
 """
 import numpy as np
 import pytest
@@ -35,8 +37,9 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_matches_single_problem_products(lbtr, prec):
+def test_batch_matches_single_problem_products(lbtr, prec, persistent):
     p = lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED
     dt = torch.float64 if prec == "fp64" else torch.float32
     tol = 1e-12 if prec == "fp64" else 1e-6
@@ -44,6 +47,7 @@ def test_batch_matches_single_problem_products(lbtr, prec):
     probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
     batch = lbtr.lb_batch_create(probs, p)
     assert len(batch) == len(ws)
+    lbtr.lb_batch_set_launch(batch, persistent)
     phis = [torch.tensor(w.phi0, dtype=dt, device=DEV) for w in ws]
     vs = [torch.tensor(inputs.gaussian_field(w.shape, 1.0, 900 + i), dtype=dt, device=DEV) for i, w in enumerate(ws)]
     refs = []
@@ -63,8 +67,12 @@ def test_batch_matches_single_problem_products(lbtr, prec):
         torch.cuda.synchronize()
         for i, (h, r) in enumerate(zip(hvs, refs)):
             assert _rel(h.double().cpu().numpy(), r.double().cpu().numpy()) <= tol, (call, i)
-    # two members against the oracle (parity tolerances)
-    for i in (0, len(ws) - 2):
+    # one member of every grid size (the 2D ones run in the persistent launch, the 3D ones
+    # as graph branches) against the oracle (parity tolerances)
+    first = {}
+    for i, w in enumerate(ws):
+        first.setdefault(w.shape, i)
+    for i in sorted(first.values()):
         w = ws[i]
         pr = olb.Problem.from_workload(w)
         ref = olb.hessvec(pr, phis[i].double().cpu().numpy(), vs[i].double().cpu().numpy())
@@ -110,3 +118,37 @@ def test_batch_tr_solve_rejects_aliased_fields(lbtr):
     ph = torch.tensor(ws[0].phi0, dtype=torch.float64, device=DEV)
     with pytest.raises(lbtr.LBError):
         lbtr.lb_batch_tr_solve(batch, [ph, ph])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_tune_keeps_products_and_reports_its_table(lbtr, prec):
+    p = lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ws = inputs.batched_sweep(24, seed=5, sizes=(64, 128, 256, 512))
+    probs = [(w.dim, w.shape[0], list(w.box)[::-1], w.xi, w.tau, w.gamma) for w in ws]
+    batch = lbtr.lb_batch_create(probs, p)
+    phis = [torch.tensor(w.phi0, dtype=dt, device=DEV) for w in ws]
+    vs = [torch.tensor(inputs.gaussian_field(w.shape, 1.0, 700 + i), dtype=dt, device=DEV) for i, w in enumerate(ws)]
+    hvs = [torch.empty_like(v) for v in vs]
+    lbtr.lb_batch_hessvec(batch, phis, vs, hvs)
+    torch.cuda.synchronize()
+    before = [h.clone() for h in hvs]
+    table = lbtr.lb_batch_tune(batch, phis, vs, hvs, replays=3)
+    cands = table["candidates"]
+    assert len(cands) >= 3 and cands[0]["strategy"] == "grouped"
+    assert any(c["strategy"] == "persistent" for c in cands)
+    assert all(c["us"] > 0 and c["row_blocks_per_task"] in (1, 4) for c in cands)
+    assert all(c["ctas_per_sm"] >= 1 for c in cands if c["strategy"] == "persistent")
+    best = min(range(len(table["candidates"])), key=lambda k: table["candidates"][k]["us"])
+    assert table["chosen"] == best
+    for h in hvs:
+        h.fill_(float("nan"))
+    lbtr.lb_batch_hessvec(batch, phis, vs, hvs)           # records anew with the chosen launch
+    torch.cuda.synchronize()
+    for h, r in zip(hvs, before):
+        # the grouped launches and the persistent one sum F''(phi) v in different orders
+        assert _rel(h.double().cpu().numpy(), r.double().cpu().numpy()) <= (1e-12 if prec == "fp64" else 1e-6)
+    w = ws[-1]
+    pr = olb.Problem.from_workload(w)
+    ref = olb.hessvec(pr, phis[-1].double().cpu().numpy(), vs[-1].double().cpu().numpy())
+    assert _rel(hvs[-1].double().cpu().numpy(), ref) <= (1e-12 if prec == "fp64" else 2e-5)
