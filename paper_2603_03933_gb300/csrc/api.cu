@@ -1,4 +1,5 @@
 // C ABI of the LB IMEX-TR library: contexts and the per-call drivers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -136,6 +137,50 @@ lb_status lb_profile_read(lb_ctx* ctx, int kclass, double* total_ms, long long* 
     if (total_ms) *total_ms = ctx->prof.ms(kclass);
     if (launches) *launches = ctx->prof.launches(kclass);
     if (alg_bytes) *alg_bytes = ctx->prof.bytes(kclass);
+    return LB_OK;
+}
+
+// FP64 FMA throughput probe: every thread runs 8 independent chains of dependent fused
+// multiply-adds (enough in flight per warp to hide the FP64 pipe latency); the result is
+// written only under a condition that never holds, so the loop cannot be removed.
+__global__ void k_fp64_fma_loop(double* sink, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1e-9 * (double)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += x[k];
+    if (t == -1.0) sink[0] = t;
+}
+
+lb_status lb_measure_fp64_rate(double* tflops, lb_stream stream) {
+    if (!tflops) return LB_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LB_ERR_CUDA;
+    const int blocks = 8 * nsm, threads = 256, iters = 4096;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LB_ERR_CUDA;
+    double best = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {      // the first run is a warm-up
+        cudaEventRecord(e0, s);
+        k_fp64_fma_loop<<<blocks, threads, 0, s>>>(nullptr, iters, 0.9999999, 1e-7);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return LB_ERR_CUDA; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (rep > 0 && ms > 0.0f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    *tflops = best;
     return LB_OK;
 }
 
