@@ -9,6 +9,8 @@ Readings of the paper taken here (all listed in the design notes):
     with G(s) = 1/2 sum_k Lambda_k |s_hat_k|^2, which avoids the cancellation of a
     difference of two O(1e-2) energies; `energy_drop_direct` keeps the literal form.
   * "||s_j|| = nu_j" is read as | ||s_j|| - nu_j | <= 1e-12 nu_j.
+  * "lambda_j <= mu_j ||s_j||" is evaluated as lambda_j / ||s_j|| <= mu_j, the form of the
+    mu update, so that after that update the test holds as the algorithm intends.
   * mu: the update Algorithm 1 makes when the previous ratio failed acts on the running mu;
     the CONTRACT branch leaves mu unchanged.
   * CONTRACT's linear systems (H + lambda~ I) s = -g are solved by preconditioned CG
@@ -123,6 +125,21 @@ def contract(p: lb.Problem, v, g, r, mu, s_j, lam_j, prm, log=None):
     return prm["gamma_c"] * sn
 
 
+def step_kind(rho: float, lam_j: float, sn: float, mu: float, nu: float, prm: dict) -> str:
+    """The three branches of Algorithm 1 for the step s_j (||s_j|| = sn, multiplier lam_j):
+    "accept" when rho_j >= theta and (lam_j <= mu_j ||s_j|| or ||s_j|| = nu_j); "contract"
+    when rho_j < theta; "shrink" otherwise.  lam_j <= mu_j ||s_j|| is evaluated as
+    lam_j / ||s_j|| <= mu_j, the form in which mu_j = max(mu, lam_j / ||s_j||) is updated after
+    a failed ratio, so that the update's guarantee (the test then holds) survives rounding:
+    the product form can miss by one ulp, and the shrink branch would then set
+    r = lam_j / mu_j = ||s_j||, the same subproblem again."""
+    if rho >= prm["theta"] and (lam_j / sn <= mu or abs(sn - nu) <= 1e-12 * nu):
+        return "accept"
+    if rho < prm["theta"]:
+        return "contract"
+    return "shrink"
+
+
 def imex_tr(p: lb.Problem, v0: np.ndarray, params: dict | None = None, max_outer: int = 500,
             eps: float | None = None, second_order: bool = True, tol2: float = 1e-8,
             max_inner: int = 20000, eps_sub: float | None = None, seed: int = 0,
@@ -171,18 +188,16 @@ def imex_tr(p: lb.Problem, v0: np.ndarray, params: dict | None = None, max_outer
         if j > 0 and rho_prev is not None and rho_prev < prm["theta"]:
             mu = max(mu, lam_j / sn)
         rho = energy_drop(p, v, g, s) / sn ** 3
-        step = "accept"
-        if rho >= prm["theta"] and (lam_j <= mu * sn or abs(sn - nu) <= 1e-12 * nu):
+        step = step_kind(rho, lam_j, sn, mu, nu, prm)
+        if step == "accept":
             v = v + s
             nu_new = max(nu, prm["gamma_e"] * sn)
             r = min(nu_new, max(r, prm["gamma_e"] * sn))
             mu = max(mu, lam_j / sn)
             nu = nu_new
-        elif rho < prm["theta"]:
-            step = "contract"
+        elif step == "contract":
             r = contract(p, v, g, r, mu, s, lam_j, prm)
         else:
-            step = "shrink"
             r = min(nu, lam_j / mu)
         rho_prev = rho
         if log is not None:

@@ -435,7 +435,10 @@ lb_status lb_ctx::tr_solve(double* v, const lb_tr_opts& o, lb_tr_info* info, cud
         if ((st = sync_read(&R, P.slot(S_RED1), 1, s, "ratio"))) return st;
         const double drop = -(gs + Gs + R / n);
         const double rho = drop / (sn * sn * sn);
-        if (rho >= o.theta && (lam <= S.mu * sn || std::fabs(sn - S.nu) <= 1e-12 * S.nu)) {
+        // lambda <= mu ||s|| in the form of the mu update above (lambda / ||s|| <= mu), so that
+        // after that update the test holds exactly as Algorithm 1 intends; the product form
+        // can miss by one ulp and the shrink branch would then repeat the same subproblem
+        if (rho >= o.theta && (lam / sn <= S.mu || std::fabs(sn - S.nu) <= 1e-12 * S.nu)) {
             P.axpby(v, sd, 1.0, 1.0, s);
             const double nu_new = std::max(S.nu, o.gamma_e * sn);
             S.r = std::min(nu_new, std::max(S.r, o.gamma_e * sn));

@@ -239,3 +239,22 @@ def test_tr_step_contract_then_mu_update_forces_accept():
     assert e1["mu"] == pytest.approx(e1["lambda"] / e1["snorm"], rel=1e-12)
     assert e1["r"] == pytest.approx(min(5.0, max(e0["r"], 2.0 * e1["snorm"])), rel=1e-12)
     assert e1["nu"] == pytest.approx(max(5.0, 2.0 * e1["snorm"]), rel=1e-12)
+
+
+def test_step_kind_accepts_after_the_mu_update_despite_rounding():
+    # Algorithm 1: after a failed ratio mu_j = max(mu, lambda_j / ||s_j||), so lambda_j <=
+    # mu_j ||s_j|| holds and a step with rho_j >= theta is accepted.  For this pair the product
+    # (lambda / s) * s rounds one ulp below lambda; evaluated as a product the test would
+    # fail and the shrink branch would return r = lambda / mu = ||s||, the same subproblem.
+    prm = dict(tr.PAPER_PARAMS)
+    lam, sn = 0.21659939713061338, 0.4221165755827173
+    mu = max(0.5, lam / sn)                          # the update after a failed ratio
+    assert (lam / sn) * sn < lam                     # the rounding the test guards against
+    assert tr.step_kind(0.5, lam, sn, mu, 5.0, prm) == "accept"
+    # the other branches: a failed ratio contracts; lambda / ||s|| above mu (and ||s|| < nu)
+    # shrinks; ||s|| = nu accepts whatever lambda is
+    assert tr.step_kind(1e-5, lam, sn, mu, 5.0, prm) == "contract"
+    assert tr.step_kind(0.5, lam, sn, 0.99 * lam / sn, 5.0, prm) == "shrink"
+    assert tr.step_kind(0.5, lam, sn, 0.99 * lam / sn, sn, prm) == "accept"
+    assert tr.step_kind(prm["theta"], lam, sn, mu, 5.0, prm) == "accept"   # rho = theta accepts
+
