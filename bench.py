@@ -295,14 +295,16 @@ def time_hvp(lbtr, ctx, pool, batch, steps, warmup, world):
     return e0.elapsed_time(e1) / 1000.0
 
 
-def time_tr(lbtr, w, prec: str, outer: int) -> dict:
+def time_tr(lbtr, w, prec: str, outer: int, persistent: bool = True) -> dict:
     """Outer IMEX-TR iterations per second on the workload from its initial field.
 
     Both precisions solve every subproblem to the same relative residual (1e-6 of
-    ||g||) so the comparison is at equal inner accuracy."""
+    ||g||) so the comparison is at equal inner accuracy.  `persistent`: the one-launch
+    inner loop where the library has it (128^3 mixed), else per-iteration launches."""
     import torch
     ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
                                         lbtr.LB_MIXED if prec == "mixed" else lbtr.LB_FP64)
+    lbtr.lb_set_persistent_subproblem(ctx, persistent)
     o = lbtr.default_tr_opts()
     o.eps = 1e-8
     o.sub.eps_sub = 0.0
@@ -326,6 +328,12 @@ def time_tr(lbtr, w, prec: str, outer: int) -> dict:
            "energy": info["energy"], "gmax": info["gmax"], "sub_rel_tol": 1e-6,
            "sub_stalled": info["sub_stalled"], "sub_capped": info["sub_capped"],
            "sub_worst_rel_res": info["sub_worst_rel_res"],
+           "inner_loop": ("one launch per subproblem" if lbtr.lb_persistent_subproblem_available(ctx)
+                          else "launches per inner iteration"),
+           # an inner iteration must at least read phi and g and read and write the iterate:
+           # 16 N bytes in float, 32 N in double (the one-launch form keeps them in L2)
+           "inner_alg_bytes": (16 if prec == "mixed" else 32) * w.n_points,
+           "inner_alg_gbs": (16 if prec == "mixed" else 32) * w.n_points * info["inner"] / dt / 1e9,
            "note": "outer iterations from the initial field, not a solve"}
     # per-kernel-class breakdown of one more outer iteration (CUDA events per launch)
     phi = torch.tensor(w.phi0, dtype=torch.float64, device="cuda")
@@ -648,6 +656,13 @@ def main():
     if args.tr_outer > 0:
         for prec in ("mixed", "fp64"):
             tr[prec] = time_tr(lbtr, w, prec, args.tr_outer if prec == "mixed" else max(1, args.tr_outer // 2))
+        # the same mixed outer iterations with the inner loop as per-iteration launches
+        tr["mixed_per_iteration_launches"] = time_tr(lbtr, w, "mixed", args.tr_outer, persistent=False)
+        tr["mixed_per_iteration_launches"].pop("profiled_outer_iteration", None)
+        tr["inner_speedup_one_launch"] = (tr["mixed"]["inner_iters_per_s"] /
+                                          tr["mixed_per_iteration_launches"]["inner_iters_per_s"])
+        for k in ("mixed", "fp64", "mixed_per_iteration_launches"):
+            tr[k]["inner_frac_of_hbm"] = tr[k]["inner_alg_gbs"] / peaks["hbm_gbs"]
     tr_solve = None
     if not args.no_solve:
         try:

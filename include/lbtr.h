@@ -434,6 +434,18 @@ lb_status lb_batch_tr_solve(lb_batch *batch, double *const *phi, const lb_tr_opt
  * Synchronises the stream. */
 lb_status lb_measure_fp64_rate(double *tflops, lb_stream stream);
 
+/* Inner loop of lb_tr_subproblem (and of the subproblems of lb_imex_tr_solve) on 3D
+ * 128^3 grids in LB_MIXED precision (Algorithm 3, §3.2): with `enable` != 0 (the default)
+ * the whole solve -- b_0, every iteration with its stop test and multiplier rule, and the
+ * returned iterate -- runs as ONE cooperative launch whose CTAs take the same decisions
+ * from the same grid-wide sums; with 0, each iteration is two launches and the host polls
+ * the device state between chunks of iterations.  Both follow the same tests and give the
+ * same iterates up to summation order.  Other grids and precisions always take the
+ * per-iteration launches.  lb_persistent_subproblem_available sets *available to 1 when the
+ * context's grid and device admit the one-launch form and it is enabled. */
+lb_status lb_set_persistent_subproblem(lb_ctx *ctx, int enable);
+lb_status lb_persistent_subproblem_available(lb_ctx *ctx, int *available);
+
 /* Test hook: cap on the device-side spin of grid barriers, in SM clock cycles
  * (0 restores the default of about two seconds).  Lets tests exercise the
  * LB_ERR_TIMEOUT path without a hang. */

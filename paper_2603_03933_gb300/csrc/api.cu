@@ -191,6 +191,20 @@ lb_status lb_set_barrier_budget(lb_ctx* ctx, long long cycles) {
     return LB_OK;
 }
 
+lb_status lb_set_persistent_subproblem(lb_ctx* ctx, int enable) {
+    if (!ctx) return LB_ERR_INVALID_ARG;
+    if (ctx->p32) ctx->p32->set_imex_persistent(enable != 0);
+    if (ctx->p64) ctx->p64->set_imex_persistent(enable != 0);
+    return LB_OK;
+}
+
+lb_status lb_persistent_subproblem_available(lb_ctx* ctx, int* available) {
+    if (!ctx || !available) return LB_ERR_INVALID_ARG;
+    *available = (ctx->p32 && ctx->p32->imex_persistent_available()) ||
+                 (ctx->p64 && ctx->p64->imex_persistent_available());
+    return LB_OK;
+}
+
 lb_status lb_energy_grad(lb_ctx* ctx, const void* phi, double* energy, void* grad, double* gmax,
                          lb_stream stream) {
     if (!ctx || !phi || !energy) return fail(ctx, LB_ERR_INVALID_ARG, "lb_energy_grad: null argument");

@@ -149,9 +149,19 @@ struct lb_ctx {
         double dscale = d0 ? 0.0 : -r / gnorm;
         cudaMemcpyAsync(d_scal, &dscale, sizeof(double), cudaMemcpyHostToDevice, s);
         p.reset_barrier(s);
+        lbtr::ImexState hs;
+        if (p.imex_persistent_available()) {
+            // the whole inner loop and the returned iterate in one launch
+            p.imex_persistent(phi, g, d0, d_scal, d, r, o.eps_sub, o.rel_tol * gnorm, o.max_iter, s);
+            if ((st = launch_status("lb_tr_subproblem/persistent"))) return st;
+            cudaMemcpyAsync(&hs, p.imex_state(), sizeof(hs), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { err = std::string("lb_tr_subproblem: ") + cudaGetErrorString(e); return LB_ERR_CUDA; }
+            if (p.read_error(s)) { err = "lb_tr_subproblem: a grid barrier timed out"; return LB_ERR_TIMEOUT; }
+            if (!hs.done) { err = "lb_tr_subproblem: the persistent solve ended without a result"; return LB_ERR_CUDA; }
+        } else {
         p.imex_init(phi, g, d0, d_scal, r, o.eps_sub, o.rel_tol * gnorm, o.max_iter, s);
         if ((st = launch_status("lb_tr_subproblem/init"))) return st;
-        lbtr::ImexState hs;
         int j = 1;
         int chunk = 2;     // chunks grow 2, 4, 8, ... up to check_every: little work is wasted
                            // on no-op launches after an early convergence
@@ -172,6 +182,7 @@ struct lb_ctx {
         }
         p.imex_final(d, s);
         if ((st = launch_status("lb_tr_subproblem/final"))) return st;
+        }
         // ||d|| and f(d) = <g,d> + <d,Hd>/2
         T* hd = static_cast<T*>(tmp_w[7]);
         p.hessvec(phi, d, hd, s);

@@ -101,45 +101,23 @@ template <typename T> __device__ __forceinline__ T h3_f2(const Model<T>& m, T u)
 }
 
 // ---------------------------------------------------------------------------------
-// phase 1: v (real plane z) -> S[z][kx][ky]; the plane's sum of F''(phi) v -> partials[z]
+// x and y forward transforms of one plane.  Thread (y = tid / 8, j = tid % 8) holds
+// u[m] = z[j + 8 m], the complex pairs z[n] = x[2n] + i x[2n+1] of row y; the plane's
+// spectrum goes to spec[z][kx][ky].  `handoff` runs once, right after the block-wide
+// hand-off barrier (the shared scratch after the hand-off buffer is then readable).
 // ---------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsigned char* smem_raw) {
+template <typename T, typename F>
+__device__ __forceinline__ void h3_fwd_xy(const cplx<T>* __restrict__ tw, cplx<T>* spec, int z,
+                                          unsigned char* smem_raw, cplx<T> (&u)[8], F&& handoff) {
     using G = H3;
     using C = cplx<T>;
     constexpr int M = G::M, H = G::H;
     C* P = reinterpret_cast<C*>(smem_raw);                   // [64][PS]
     C* ws = P + H * G::PS + (threadIdx.x >> 5) * G::WS;      // this warp's scratch
-    double* red = reinterpret_cast<double*>(P + H * G::PS + 32 * G::WS);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const C* __restrict__ tw = a.tw;
     const int y = tid >> 3, j = tid & 7;                     // x: row y, thread j holds z[j + 8 m]
     const int c = tid >> 4, t = tid & 15;                    // y: column c, thread t holds Y[t + 16 m]
     const C tw2j = __ldg(&tw[2 * j]), twj = __ldg(&tw[j]), twt = __ldg(&tw[t]);
-    const size_t row = (size_t)z * M + y;
-    C u[8], p[8];
-    {
-        const C* vr = reinterpret_cast<const C*>(a.v) + row * H;
-        const C* pr = reinterpret_cast<const C*>(a.phi) + row * H;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) { u[m] = vr[j + 8 * m]; p[m] = pr[j + 8 * m]; }
-    }
-    {
-        // w = F''(phi) v, kept in shared memory for phase 3; the thread's 16 terms of the
-        // projection sum in the working precision, then the warp's total in double-word form;
-        // warp totals are added after the hand-off barrier
-        T sum = (T)0;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            sum = fma(h3_f2(a.model, p[m].x), u[m].x, sum);
-            sum = fma(h3_f2(a.model, p[m].y), u[m].y, sum);
-        }
-        Acc<T> acc;
-        acc.add(sum);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc.add_shfl(off);
-        if (lane == 0) red[warp] = acc.get();
-    }
     dft_r<-1, 8, T>(u);                                      // over m
     {
         C w[8];
@@ -179,13 +157,7 @@ __device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsign
         for (int k2 = 0; k2 < 8; ++k2) P[(j + 8 * k2) * G::PS + y] = out[k2];
     }
     __syncthreads();
-    if (warp == 1) {
-        // the plane's projection sum: the 32 warp totals in a fixed order
-        double q = red[lane];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
-        if (lane == 0) a.partials[z] = q;
-    }
+    handoff();
 
     // ---- y ----
     C x[8];
@@ -220,7 +192,7 @@ __device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsign
         }
     }
     // thread (aa, t1) of column c now holds Y[ky] for ky = aa + 8 k + 64 t1 at x[k]
-    C* S = a.spec + (size_t)z * G::NKX * M;
+    C* S = spec + (size_t)z * G::NKX * M;
     if (c != 0) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) S[(size_t)c * M + aa + 8 * k + 64 * t1] = x[k];
@@ -247,27 +219,67 @@ __device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsign
 }
 
 // ---------------------------------------------------------------------------------
-// phase 2: four z lines (task q: lines 4q..4q+3 of kx * M + ky), forward transform,
-// Lambda / N with k = 0 removed, inverse transform, in place; ts: the warp's scratch
+// phase 1: v (real plane z) -> S[z][kx][ky]; the plane's sum of F''(phi) v -> partials[z]
 // ---------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cplx<T>* ts) {
+__device__ __forceinline__ void h3_fwd_plane(const Hvp3Args<T>& a, int z, unsigned char* smem_raw) {
+    using G = H3;
+    using C = cplx<T>;
+    constexpr int M = G::M, H = G::H;
+    double* red = reinterpret_cast<double*>(reinterpret_cast<C*>(smem_raw) + H * G::PS + 32 * G::WS);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int y = tid >> 3, j = tid & 7;
+    const size_t row = (size_t)z * M + y;
+    C u[8], p[8];
+    {
+        const C* vr = reinterpret_cast<const C*>(a.v) + row * H;
+        const C* pr = reinterpret_cast<const C*>(a.phi) + row * H;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) { u[m] = vr[j + 8 * m]; p[m] = pr[j + 8 * m]; }
+    }
+    {
+        // the thread's 16 terms of the projection sum of F''(phi) v in the working precision,
+        // then the warp's total in double-word form; warp totals are added after the hand-off
+        T sum = (T)0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            sum = fma(h3_f2(a.model, p[m].x), u[m].x, sum);
+            sum = fma(h3_f2(a.model, p[m].y), u[m].y, sum);
+        }
+        Acc<T> acc;
+        acc.add(sum);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc.add_shfl(off);
+        if (lane == 0) red[warp] = acc.get();
+    }
+    h3_fwd_xy<T>(a.tw, a.spec, z, smem_raw, u, [&]() {
+        if (warp == 1) {
+            // the plane's projection sum: the 32 warp totals in a fixed order
+            double q = red[lane];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+            if (lane == 0) a.partials[z] = q;
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------------
+// z lines of task q (lines 4q..4q+3 of kx * M + ky): four lines per warp, thread i of line l
+// (lane = 4 i + l).  h3_zfwd loads and transforms them (v[s * 8 + b] = X[kz], kz = i + 8 s +
+// 16 b); h3_zinv transforms back and stores in place.  ts: the warp's scratch.
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void h3_zfwd(const cplx<T>* __restrict__ tw, const cplx<T>* spec, int task, cplx<T>* ts,
+                                        cplx<T> (&v)[16]) {
     using G = H3;
     using C = cplx<T>;
     constexpr int M = G::M, NL = G::NLINES;
     const int lane = threadIdx.x & 31;
-    const int l = lane & 3, i = lane >> 2;                   // line of the warp, thread within the line
-    const int line = task * 4 + l;                           // kx * M + ky
-    const int kx = line >> 7, ky = line & (M - 1);
-    const C* __restrict__ tw = a.tw;
-    const T* __restrict__ qt = a.qtab;
+    const int l = lane & 3, i = lane >> 2;
+    const C* base = spec + task * 4 + l;
     const C twi = __ldg(&tw[i]);
-    const T bxy = __ldg(&qt[kx]) + __ldg(&qt[M + ky]);
-    C* base = a.spec + line;
-    C v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = base[(size_t)(i + 8 * m) * NL];
-    const T qzc = __ldg(&qt[2 * M + 1]);                     // (2 pi / L_z)^2: |Bk|^2 of kz is qzc * k^2
     // forward: DFT16 over m, twiddle W_M^{i q}, transpose, DFT8 over i
     dft_r<-1, 16, T>(v);
     {
@@ -293,21 +305,18 @@ __device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cp
         for (int ii = 0; ii < 8; ++ii) v[s * 8 + ii] = tl[q * 9 + ii];
         dft_r<-1, 8, T>(&v[s * 8]);
     }
-    // v[s * 8 + b] = X[kz = i + 8 s + 16 b]
-    {
-        const bool k0 = (kx == 0 && ky == 0);
-#pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const int kz = i + 8 * s + 16 * b;
-                const T kk = (T)(kz < M / 2 ? kz : kz - M);
-                const T tt = (T)1 - (bxy + qzc * (kk * kk));
-                T f = a.xi2 * tt * tt * a.kscale;
-                if (k0 && kz == 0) f = (T)0;
-                v[s * 8 + b] = mk<T>(v[s * 8 + b].x * f, v[s * 8 + b].y * f);
-            }
-    }
+}
+
+template <typename T>
+__device__ __forceinline__ void h3_zinv(const cplx<T>* __restrict__ tw, cplx<T>* spec, int task, cplx<T>* ts,
+                                        cplx<T> (&v)[16]) {
+    using G = H3;
+    using C = cplx<T>;
+    constexpr int NL = G::NLINES;
+    const int lane = threadIdx.x & 31;
+    const int l = lane & 3, i = lane >> 2;
+    const C twi = __ldg(&tw[i]);
+    C* tl = ts + l * G::ZTS;
     // inverse: DFT8 over b, twiddle W_M^{-c q} (q = i + 8 s), transpose back, DFT16
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -332,25 +341,59 @@ __device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cp
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = tl[q * 9 + i];
     dft_r<+1, 16, T>(v);
+    C* base = spec + task * 4 + l;
 #pragma unroll
     for (int m = 0; m < 16; ++m) base[(size_t)(i + 8 * m) * NL] = v[m];
     __syncwarp();                                            // the scratch is free for the next task
 }
 
-// ---------------------------------------------------------------------------------
-// phase 3: S[z][kx][ky] -> Hv (real plane z) with F''(phi) v - mean
-// ---------------------------------------------------------------------------------
+// phase 2 of the product: forward, Lambda / N with k = 0 removed, inverse
 template <typename T>
-__device__ __forceinline__ void h3_inv_plane(const Hvp3Args<T>& a, int z, unsigned char* smem_raw) {
+__device__ __forceinline__ void h3_zline_task(const Hvp3Args<T>& a, int task, cplx<T>* ts) {
+    using G = H3;
+    using C = cplx<T>;
+    constexpr int M = G::M;
+    const int lane = threadIdx.x & 31;
+    const int l = lane & 3, i = lane >> 2;
+    const int line = task * 4 + l;                           // kx * M + ky
+    const int kx = line >> 7, ky = line & (M - 1);
+    const T* __restrict__ qt = a.qtab;
+    const T bxy = __ldg(&qt[kx]) + __ldg(&qt[M + ky]);
+    const T qzc = __ldg(&qt[2 * M + 1]);                     // (2 pi / L_z)^2: |Bk|^2 of kz is qzc * k^2
+    C v[16];
+    h3_zfwd<T>(a.tw, a.spec, task, ts, v);
+    {
+        const bool k0 = (kx == 0 && ky == 0);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int kz = i + 8 * s + 16 * b;
+                const T kk = (T)(kz < M / 2 ? kz : kz - M);
+                const T tt = (T)1 - (bxy + qzc * (kk * kk));
+                T f = a.xi2 * tt * tt * a.kscale;
+                if (k0 && kz == 0) f = (T)0;
+                v[s * 8 + b] = mk<T>(v[s * 8 + b].x * f, v[s * 8 + b].y * f);
+            }
+    }
+    h3_zinv<T>(a.tw, a.spec, task, ts, v);
+}
+
+// ---------------------------------------------------------------------------------
+// y and x inverse transforms of one plane: spec[z][kx][ky] -> u[m] = z[j + 8 m] of row
+// y = tid / 8 (unscaled).  `early` runs once between the column loads and the first
+// exchange (the shared scratch after the hand-off buffer is free then).
+// ---------------------------------------------------------------------------------
+template <typename T, typename F>
+__device__ __forceinline__ void h3_inv_xy(const cplx<T>* __restrict__ tw, const cplx<T>* spec, int z,
+                                          unsigned char* smem_raw, cplx<T> (&u)[8], F&& early) {
     using G = H3;
     using C = cplx<T>;
     constexpr int M = G::M, H = G::H;
     C* P = reinterpret_cast<C*>(smem_raw);
     C* ws = P + H * G::PS + (threadIdx.x >> 5) * G::WS;
-    T* s_mean = reinterpret_cast<T*>(P + H * G::PS + 32 * G::WS);
     const int tid = threadIdx.x, lane = tid & 31;
-    const C* __restrict__ tw = a.tw;
-    const C* S = a.spec + (size_t)z * G::NKX * M;
+    const C* S = spec + (size_t)z * G::NKX * M;
     const int c = tid >> 4, t = tid & 15, aa = t >> 1, t1 = t & 1;
     const int y = tid >> 3, j = tid & 7;
     const C tw2j = __ldg(&tw[2 * j]), twj = __ldg(&tw[j]), twt = __ldg(&tw[t]);
@@ -371,15 +414,7 @@ __device__ __forceinline__ void h3_inv_plane(const Hvp3Args<T>& a, int z, unsign
             x[k] = mk<T>(e.x - f.y, e.y + f.x);
         }
     }
-    if (tid >= 32 && tid < 64) {
-        // mean of F''(phi) v: warp 1 adds the planes' partial sums in a fixed order
-        double q = 0.0;
-#pragma unroll
-        for (int k = 0; k < M / 32; ++k) q += __ldcg(&a.partials[lane + 32 * k]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
-        if (lane == 0) *s_mean = (T)(q * a.inv_n);
-    }
+    early();
     // 2-point step between the lanes t1 = 0, 1, then W_16^{-k} on the odd half
     {
         const T sg = t1 ? (T)-1 : (T)1;
@@ -412,10 +447,8 @@ __device__ __forceinline__ void h3_inv_plane(const Hvp3Args<T>& a, int z, unsign
     __syncthreads();
 
     // ---- x inverse: row y, thread j ----
-    C u[8];
 #pragma unroll
     for (int k2 = 0; k2 < 8; ++k2) u[k2] = P[(j + 8 * k2) * G::PS + y];
-    const size_t row = (size_t)z * M + y;
     // complex-to-real pre-step: Z[k] = (X[k] + conj X[H-k]) + i (X[k] - conj X[H-k]) conj(W_M^k)
     {
         const int partner = (lane & ~7) | ((8 - j) & 7);
@@ -456,7 +489,33 @@ __device__ __forceinline__ void h3_inv_plane(const Hvp3Args<T>& a, int z, unsign
         for (int q = 0; q < 8; ++q) u[q] = xs[j * 9 + q];
     }
     dft_r<+1, 8, T>(u);                                      // u[m] = z[j + 8 m] (unscaled)
+}
+
+// ---------------------------------------------------------------------------------
+// phase 3: S[z][kx][ky] -> Hv (real plane z) with F''(phi) v - mean
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void h3_inv_plane(const Hvp3Args<T>& a, int z, unsigned char* smem_raw) {
+    using G = H3;
+    using C = cplx<T>;
+    constexpr int M = G::M, H = G::H;
+    T* s_mean = reinterpret_cast<T*>(reinterpret_cast<C*>(smem_raw) + H * G::PS + 32 * G::WS);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int y = tid >> 3, j = tid & 7;
+    C u[8];
+    h3_inv_xy<T>(a.tw, a.spec, z, smem_raw, u, [&]() {
+        if (tid >= 32 && tid < 64) {
+            // mean of F''(phi) v: warp 1 adds the planes' partial sums in a fixed order
+            double q = 0.0;
+#pragma unroll
+            for (int k = 0; k < M / 32; ++k) q += __ldcg(&a.partials[lane + 32 * k]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+            if (lane == 0) *s_mean = (T)(q * a.inv_n);
+        }
+    });
     const T mean = *s_mean;                                  // written before the hand-off barrier
+    const size_t row = (size_t)z * M + y;
     const C* vr = reinterpret_cast<const C*>(a.v) + row * H;
     const C* pr = reinterpret_cast<const C*>(a.phi) + row * H;
     C* hr = reinterpret_cast<C*>(a.hv) + row * H;

@@ -66,6 +66,12 @@ public:
     int imex_iterate(const T* phi, const T* g, int j0, int count, cudaStream_t s);
     // d = F^{-1}(B[final_src] / (1 + eta (Lambda + final_lam)))
     void imex_final(T* d, cudaStream_t s);
+    // The whole solve (init, iterations, the returned iterate d) as one cooperative launch
+    // (k_imex3, 3D 128^3 float grids); available() is false elsewhere or when switched off.
+    bool imex_persistent_available() const { return imex3_grid_ > 0 && imex3_on_; }
+    void set_imex_persistent(bool on) { imex3_on_ = on; }
+    int imex_persistent(const T* phi, const T* g, const T* d0, const double* dscale_dev, T* d, double r,
+                        double eps_abs, double eps_rel_abs, int max_iter, cudaStream_t s);
 
     // --- spectral operators used by Lanczos ---
     // out = K q with K = M^{-1/2} H M^{-1/2} (q, out paper-normalised half spectra)
@@ -173,6 +179,8 @@ private:
     bool use_planes_ = false;
     bool hvp3_ = false;       // 3D 128^3 float products take the kernels of hvp3d.cuh
     int hvp3_grid_ = 0;       // CTAs of the fused cooperative product (0: three kernels)
+    int imex3_grid_ = 0;      // CTAs of the persistent subproblem kernel (0: not available)
+    bool imex3_on_ = true;
     int ln_grid_cap_ = 0;     // persistent grid of the pipelined column passes (0: not used)
     int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
     size_t zf_smem_ = 0;

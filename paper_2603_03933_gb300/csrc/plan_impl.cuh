@@ -8,7 +8,9 @@
 #include "lines.cuh"
 #include "rows.cuh"
 #include "imex_fused.cuh"
+#include "imex3d.cuh"
 #include "hvp3d.cuh"
+#include "sweep.cuh"
 
 namespace lbtr {
 
@@ -80,6 +82,11 @@ template <typename T, int M> cudaError_t set_lines_attrs(int* per) {
         setl((const void*)k_lines_b<T, M, C_LAM>);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_lines<T, M, C_LAM>, ln_nt(M), ln_smem<T>(M));
+    }
+    if constexpr (M == 512) {
+        cudaError_t r = cudaFuncSetAttribute((const void*)k_lines512_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sw_lines_smem<T>(512));
+        if (r != cudaSuccess) e = r;
     }
     return e;
 }
@@ -196,6 +203,18 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
         int coop = 0;
         LB_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         hvp3_grid_ = (coop && per > 0) ? nsm * per : 0;
+        if constexpr (sizeof(T) == 4) {
+            // the persistent subproblem kernel: every warp owns at most one z-line task, so
+            // the grid needs at least NTASKS / 32 CTAs
+            ea = cudaFuncSetAttribute((const void*)k_imex3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)I3_SMEM);
+            if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
+            int per3 = 0;
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, k_imex3<T>, H3::NT, I3_SMEM);
+            if (ea != cudaSuccess) { err = std::string("cudaOccupancyMaxActiveBlocksPerMultiprocessor: ") + cudaGetErrorString(ea); return 6; }
+            const int g3 = nsm * per3;
+            imex3_grid_ = (coop && per3 > 0 && 32 * g3 >= H3::NTASKS) ? g3 : 0;
+        }
     }
     if (use_planes_) {
         LB_SWITCH_M(m_, ea = set_plane_attrs<T, M>());
@@ -281,7 +300,8 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
     size_t o_p = take(sizeof(double) * S_COUNT * SLOT_Q * (size_t)max_blocks_);
     size_t o_r = take(sizeof(double) * S_COUNT * SLOT_Q);
     size_t o_t = take(sizeof(unsigned) * S_COUNT);
-    size_t o_sp = take(sizeof(double) * (2 * 5 * (size_t)std::max(coop_blocks_, zf_grid_) + 5 * 64 + 8));
+    size_t o_sp = take(sizeof(double) * (2 * 5 * (size_t)std::max(std::max(coop_blocks_, zf_grid_), imex3_grid_) +
+                                         5 * 64 + 8));
     size_t o_bar = take(sizeof(unsigned) * BAR_WORDS);
     size_t o_err = take(sizeof(int));
     size_t o_st = take(sizeof(ImexState));
@@ -605,6 +625,10 @@ cudaError_t launch_hvp_batch(int m, int rows, int count, const XfArgs<T>* xf, co
             k_rows_fwd_b<T, M, XF_HVPMEAN><<<gx, 128, rows_smem<T, M>(), s>>>(xf);
             if constexpr (M <= 256) {
                 k_lines_b<T, M, C_LAM><<<dim3((unsigned)col_grid, (unsigned)count), ln_nt(M), ln_smem<T>(M), s>>>(ca, col_tiles);
+            } else if constexpr (M == 512) {
+                // 2D only (the caller groups 512-point problems only in 2D): one Stockham tile per CTA
+                const unsigned tiles = (unsigned)((M / 2 + sw_nl(M) - 1) / sw_nl(M) + 1);
+                k_lines512_b<T><<<dim3(tiles, (unsigned)count), 128, sw_lines_smem<T>(M), s>>>(ca);
             } else {
                 e = cudaErrorInvalidValue;
             }
@@ -779,6 +803,45 @@ template <typename T> int Plan<T>::imex_iterate(const T* phi, const T* g, int j0
         secular(dst, 1, j, s);
     }
     return 0;
+}
+
+template <typename T>
+int Plan<T>::imex_persistent(const T* phi, const T* g, const T* d0, const double* dscale_dev, T* d, double r,
+                             double eps_abs, double eps_rel_abs, int max_iter, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return -1;
+    } else {
+        if (imex3_grid_ <= 0) return -1;
+        r_ = r; eps_abs_ = eps_abs; eps_rel_abs_ = eps_rel_abs; max_iter_ = max_iter;
+        rtol_ = 2e-6;
+        steptol_ = 1e-8;
+        model_.eta = (T)eta;
+        cudaMemsetAsync(d_state_, 0, sizeof(ImexState), s);
+        Imex3Args<T> a;
+        a.phi = phi; a.g = g; a.d0 = d0; a.dscale = dscale_dev; a.d = d;
+        a.spec = d_work_; a.b0 = d_b_[0]; a.b1 = d_b_[1];
+        a.tw = d_tw_; a.qtab = d_qtab_;
+        a.model = model_;
+        a.st = d_state_;
+        a.partials = reinterpret_cast<Part<T>*>(d_secpart_);
+        a.bar.count = d_bar_; a.bar.gen = d_bar_ + 32; a.bar.err = d_err_; a.bar.budget = budget_; a.bar.tree = d_bar_ + 64;
+        a.xi2 = (T)xi2_; a.eta = (T)eta; a.kscale = (T)(1.0 / (double)n_);
+        a.r = r_; a.rtol = rtol_; a.steptol = steptol_;
+        a.stall = stall_k(); a.max_iter = max_iter_;
+        const double inv_n2 = 1.0 / ((double)n_ * (double)n_);
+        a.t_thr_abs2 = (T)(eps_abs_ * eta * eps_abs_ * eta);
+        a.t_thr_rel2 = (T)(eps_rel_abs_ * eta * eps_rel_abs_ * eta);
+        a.t_r2 = (T)(r_ * r_);
+        a.t_rtol_r2 = (T)(rtol_ * r_ * r_);
+        a.t_inv_n2 = (T)inv_n2;
+        void* args[] = {&a};
+        cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_imex3<T>, dim3(imex3_grid_), dim3(H3::NT), args,
+                                                    I3_SMEM, s);
+        if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+        if (prof_) prof_->end(K_COLI, e0, s, 0.0);
+        return 0;
+    }
 }
 
 template <typename T> void Plan<T>::imex_final(T* d, cudaStream_t s) {

@@ -114,6 +114,8 @@ SIGNATURES = [
     ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
+    ("lb_set_persistent_subproblem", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("lb_persistent_subproblem_available", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("lb_measure_fp64_rate", ctypes.c_int, [_DP, _VP]),
     ("lb_hessvec_noalloc", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, _VP, _VP, _VP, _VP]),
     ("lb_batch_create", ctypes.c_int, [ctypes.POINTER(lb_problem), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VP)]),
@@ -362,6 +364,18 @@ def lb_sis_solve(ctx: Context, phi64, opts: lb_sis_opts | None = None, stream=No
 
 def lb_set_barrier_budget(ctx: Context, cycles: int):
     _check(ctx, load().lb_set_barrier_budget(ctx.handle, int(cycles)), "lb_set_barrier_budget")
+
+
+def lb_set_persistent_subproblem(ctx: Context, enable: bool):
+    """One-launch inner loop of the subproblem on 128^3 mixed grids (default on)."""
+    _check(ctx, load().lb_set_persistent_subproblem(ctx.handle, 1 if enable else 0), "lb_set_persistent_subproblem")
+
+
+def lb_persistent_subproblem_available(ctx: Context) -> bool:
+    out = ctypes.c_int()
+    _check(ctx, load().lb_persistent_subproblem_available(ctx.handle, ctypes.byref(out)),
+           "lb_persistent_subproblem_available")
+    return bool(out.value)
 
 
 def lb_measure_fp64_rate(stream=None) -> float:

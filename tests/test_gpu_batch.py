@@ -27,7 +27,7 @@ def lbtr():
 
 
 def _members():
-    ws = inputs.batched_sweep(10, seed=11, sizes=(16, 32, 64, 128, 256))
+    ws = inputs.batched_sweep(12, seed=11, sizes=(16, 32, 64, 128, 256, 512))
     ws.append(inputs.random_problem((32, 32, 32), 12, sigma=0.3, box=(5.0, 6.0, 7.0)))
     ws.append(inputs.random_problem((64, 64, 64), 13, sigma=0.3))
     return ws

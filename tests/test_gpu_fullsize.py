@@ -1,8 +1,8 @@
 """Parity with the FP64 oracle on the kernel paths of the full-size workloads.
 
-The subproblem kernels that the 64^3-256^3 workloads take (the cooperative fused IMEX
-kernel with register-resident columns in float at 128^3, the shared-memory or unfused
-column paths in double) are compared with the oracle's Algorithm 3 over a fixed number
+The subproblem kernels that the 64^3-256^3 workloads take (at 128^3 in float the one-launch
+inner loop and, switched off, the cooperative fused IMEX kernel with register-resident
+columns; the shared-memory or unfused column paths in double) are compared with the oracle's Algorithm 3 over a fixed number
 of iterations: eps_sub = rel_tol = 0 and max_iter = K on both sides, so both return d_K,
 and d_K, lambda_K and the residual are compared element by element.  The oracle runs on
 the same (float-rounded, in the mixed case) inputs in FP64.
@@ -51,7 +51,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def _fixed_iterations(lbtr, w, prec, r):
+def _fixed_iterations(lbtr, w, prec, r, persistent=True):
     dt = torch.float64 if prec == "fp64" else torch.float32
     phi_t = torch.tensor(w.phi0, dtype=dt, device=DEV)
     phi_in = phi_t.double().cpu().numpy()
@@ -61,6 +61,7 @@ def _fixed_iterations(lbtr, w, prec, r):
     g_in = g_t.double().cpu().numpy()
     ctx = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
                                         lbtr.LB_FP64 if prec == "fp64" else lbtr.LB_MIXED)
+    lbtr.lb_set_persistent_subproblem(ctx, persistent)
     o = lbtr.default_sub_opts()
     o.eps_sub = 0.0
     o.rel_tol = 0.0
@@ -71,11 +72,16 @@ def _fixed_iterations(lbtr, w, prec, r):
     return info, d.double().cpu().numpy(), ref
 
 
-@pytest.mark.parametrize("shape,prec,r", [((128, 128, 128), "mixed", 1.0), ((64, 64, 64), "fp64", 1.0),
-                                          ((128, 128, 128), "fp64", 1.0), ((64, 64, 64), "mixed", 0.3)])
-def test_subproblem_fixed_iterations_match_oracle(lbtr, shape, prec, r):
+@pytest.mark.parametrize("shape,prec,r,persistent", [((128, 128, 128), "mixed", 1.0, True),
+                                                     ((128, 128, 128), "mixed", 1.0, False),
+                                                     ((64, 64, 64), "fp64", 1.0, True),
+                                                     ((128, 128, 128), "fp64", 1.0, True),
+                                                     ((64, 64, 64), "mixed", 0.3, True)])
+def test_subproblem_fixed_iterations_match_oracle(lbtr, shape, prec, r, persistent):
+    # at 128^3 mixed: the one-launch inner loop (k_imex3) and the per-iteration launches
+    # (k_plane_mid + k_imex_lines); elsewhere the per-iteration launches
     w = inputs.config_3d_scale(shape[0]) if shape[0] == 128 else inputs.config_3d_bcc(shape[0])
-    info, d, ref = _fixed_iterations(lbtr, w, prec, r)
+    info, d, ref = _fixed_iterations(lbtr, w, prec, r, persistent)
     assert info["status"] == 4 and not info["converged"] and not info["stalled"]
     assert info["iterations"] == ref["iterations"] == K
     p = olb.Problem.from_workload(w)

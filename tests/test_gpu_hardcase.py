@@ -4,7 +4,9 @@ once with the deterministic inner start -r g / ||g|| only and once with a random
 every subproblem whose g^(1) (the component of g along the eigenvector of a negative
 lambda_min) is below 1e-12.  The symmetric start makes g^(1) vanish, so the deterministic
 run cannot leave the symmetric subspace and stops at a point that is not an SP-II; the
-randomized run reaches the HEX phase, an SP-II, at the paper's energy E = -1.32e-2.
+randomized run reaches the HEX phase, an SP-II, at the paper's energy E = -1.32e-2.  Both
+runs are made at two resolutions of the same box (32^3 and 64^3), so that the end states
+are properties of the iteration and not of one grid.
 """
 import numpy as np
 import pytest
@@ -24,8 +26,8 @@ def lbtr():
     return mod
 
 
-def _solve(lbtr, hard_tol):
-    w = inputs.table2_phase("LAM", 32)
+def _solve(lbtr, hard_tol, M):
+    w = inputs.table2_phase("LAM", M)
     c = lbtr.lb_create_from_array_box(w.shape, w.box, 1.0, -0.09, 0.34, lbtr.LB_FP64)
     phi = torch.tensor(w.phi0, dtype=torch.float64, device=DEV)
     o = lbtr.default_tr_opts()
@@ -39,11 +41,12 @@ def _solve(lbtr, hard_tol):
     lam = lbtr.lb_lambda_min(c, phi)["lambda_min"]
     x = phi.cpu().numpy()
     amp = np.sort(np.abs(np.fft.fftn(x) / x.size).ravel())[::-1]
-    return info, lam, amp
+    return info, lam, amp, x
 
 
-def test_randomized_start_on_nearly_hard_subproblems_reaches_hex(lbtr):
-    info, lam, amp = _solve(lbtr, 1e-12)
+@pytest.mark.parametrize("M", [32, 64])
+def test_randomized_start_on_nearly_hard_subproblems_reaches_hex(lbtr, M):
+    info, lam, amp, _ = _solve(lbtr, 1e-12, M)
     assert info["status"] == 0 and info["gmax"] < 1e-8
     assert info["randomized"] >= 1 and info["g1_min"] <= 1e-12
     assert lam >= -1e-8                                   # SP-II
@@ -52,7 +55,12 @@ def test_randomized_start_on_nearly_hard_subproblems_reaches_hex(lbtr):
     assert np.allclose(amp[:6], amp[0], rtol=1e-6) and amp[6] < 0.05 * amp[0]
 
 
-def test_deterministic_start_stops_at_a_point_that_is_not_sp2(lbtr):
-    info, lam, _ = _solve(lbtr, 0.0)
+@pytest.mark.parametrize("M", [32, 64])
+def test_deterministic_start_stops_at_a_point_that_is_not_sp2(lbtr, M):
+    info, lam, _, x = _solve(lbtr, 0.0, M)
     assert info["status"] == 0 and info["randomized"] == 0
-    assert lam < -1e-3
+    # the point reached is the disordered state phi = 0: a critical point whose Hessian is
+    # Lambda + tau (F''(0) = tau), so lambda_min = tau = -0.09, attained on the LAM
+    # wavevectors (|B k| = 1, Lambda = 0), which lie on the grid at every resolution
+    assert np.max(np.abs(x)) < 1e-6 and abs(info["energy"]) < 1e-12
+    assert abs(lam - (-0.09)) < 1e-6
