@@ -238,8 +238,7 @@ static lb_status upload_group(lb_batch* b, BatchGroup& g, const void* const* phi
         lbtr::Plan<T>* p = sizeof(T) == 8 ? reinterpret_cast<lbtr::Plan<T>*>(b->ctx[i]->p64)
                                           : reinterpret_cast<lbtr::Plan<T>*>(b->ctx[i]->p32);
         int cg = 0, ct = 0;
-        p->hvp_args((const T*)phi[i], (const T*)v[i], (T*)hv[i], xf[q], ca[q], cg, ct, xi[q],
-                    b->ctx[i]->prob.dim == 2 && g.m == 512);
+        p->hvp_args((const T*)phi[i], (const T*)v[i], (T*)hv[i], xf[q], ca[q], cg, ct, xi[q]);
     }
     const size_t bytes = cnt * (sizeof(lbtr::XfArgs<T>) + sizeof(lbtr::ColArgs<T>) + sizeof(lbtr::XiArgs<T>));
     lb_status st = batch_cuda(b, cudaMalloc(&g.args, bytes), "lb_batch_hessvec/arguments");
@@ -272,9 +271,10 @@ static lb_status record_groups(lb_batch* b, const void* const* phi, const void* 
         lb_ctx* c = b->ctx[i];
         int m = c->prob.n, rows = 0, cg = 0, ct = 0;
         bool ok;
-        // 2D problems of 512 points per axis have no persistent line kernel; their group takes
-        // the Stockham line tiles of k_lines512_b
-        const bool any_lines = c->prob.dim == 2 && m == 512;
+        // 2D problems of 512 points per axis have no persistent line kernel: they stay branches
+        // (measured: one grouped launch of 512-point Stockham line tiles, 307 us per replay of
+        // the C4 sweep, was slower than the branches on forked streams, 262 us)
+        const bool any_lines = false;
         if (c->prec == LB_FP64) {
             lbtr::XfArgs<double> xf; lbtr::ColArgs<double> ca; lbtr::XiArgs<double> xi;
             ok = c->p64->hvp_args((const double*)phi[i], (const double*)v[i], (double*)hv[i], xf, ca, cg, ct, xi,

@@ -60,6 +60,8 @@ template <typename T> struct Imex3Args {
 
 // dynamic shared memory: the fused product's plus the block-sum scratch (32 x 5 partials)
 constexpr size_t I3_SMEM = H3::FSMEM + 32 * 5 * sizeof(double);
+// largest grid the grid sums read in one round (the host launches at most this many CTAs)
+constexpr int I3_MAXG = 256;
 
 // phase A on plane z: b = d - eta (g + F''(phi) d), forward x and y transforms into spec
 template <typename T>
@@ -100,9 +102,9 @@ __device__ __forceinline__ void i3_plane_b(const Imex3Args<T>& a, int z, bool fi
 }
 
 // Sum NQ per-CTA values over the grid.  Thread 0 of each CTA passes its CTA's totals in
-// mine[]; after the barrier, warp 0 of every CTA adds all CTAs' values in the same order
-// (lane l: CTAs l, l + 32, ..., then a fixed shuffle tree), so every CTA leaves with the same
-// totals in out[] (shared).  P: this round's [NQ][gridDim] buffer; consecutive rounds must
+// mine[]; after the barrier, warp q of every CTA adds all CTAs' values of quantity q in the
+// same order (lane l: CTAs l, l + 32, ..., then a fixed shuffle tree), so every CTA leaves
+// with the same totals in out[] (shared).  P: this round's [NQ][gridDim] buffer; consecutive rounds must
 // alternate between two buffers (a CTA writes round k + 1 only after every CTA has arrived
 // at round k + 1's barrier, i.e. has finished reading round k - 1).
 template <typename T, int NQ>
@@ -113,17 +115,22 @@ __device__ __forceinline__ bool i3_grid_sum(const GridBar& bar, Part<T>* P, cons
         for (int q = 0; q < NQ; ++q) P[q * G + blockIdx.x] = mine[q];
     }
     if (!grid_sync_acqrel(bar)) return false;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    if ((int)(threadIdx.x >> 5) < NQ) {
+        // warp q sums quantity q: every load issued before the first addition (one L2 round
+        // trip), then the fixed order of the sums (the same in every CTA)
+        const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        Part<T> x[I3_MAXG / 32];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            Part<T> s;
-            part_zero(s);
-            for (int b = lane; b < G; b += 32) s = part_add(s, part_ldcg(&P[q * G + b]));
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) s = part_add(s, part_shfl_down(s, off));
-            if (lane == 0) out[q] = s;
+        for (int k = 0; k < I3_MAXG / 32; ++k) {
+            if (lane + 32 * k < G) x[k] = part_ldcg(&P[q * G + lane + 32 * k]);
+            else part_zero(x[k]);
         }
+        Part<T> s = x[0];
+#pragma unroll
+        for (int k = 1; k < I3_MAXG / 32; ++k) s = part_add(s, x[k]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s = part_add(s, part_shfl_down(s, off));
+        if (lane == 0) out[q] = s;
     }
     __syncthreads();
     return true;
@@ -198,6 +205,7 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
         const T elp = s_elp, eta = a.eta, cw = q.wgt * a.t_inv_n2;
         const C* bold = (j & 1) ? a.b0 : a.b1;               // b_{j-1}
         C* bnew = (j & 1) ? a.b1 : a.b0;                     // b_j
+        const int lane = threadIdx.x & 31;
         C v[16];
         {
             T sm[2][5] = {};
@@ -212,11 +220,6 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
                     const T ci = cw * x2;
                     const T rd = rcp_t(ai + elp), ra = rcp_t(ai);
                     const T qv = ci * rd * rd;
-                    if (check) {
-                        const C o = bold[(size_t)kz * NL + q.line];
-                        const T dx = o.x - v[e].x, dy = o.y - v[e].y;
-                        sm[e & 1][0] += q.wgt * (dx * dx + dy * dy);
-                    }
                     sm[e & 1][1] += q.wgt * x2;
                     sm[e & 1][2] += ci * ra * ra;
                     sm[e & 1][3] += qv;
@@ -226,7 +229,25 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
                 __syncwarp();
                 C* keep = scratch();
 #pragma unroll
-                for (int e = 0; e < 16; ++e) keep[e * 32 + (threadIdx.x & 31)] = v[e];
+                for (int e = 0; e < 16; ++e) keep[e * 32 + lane] = v[e];
+                if (check) {
+                    // the residual ||b_{j-1} - b_j||^2: the loads of b_{j-1} in two batches of eight
+                    // in flight at once (the lines' registers are free again), then the differences
+                    // (measured: staging them in shared memory by asynchronous copies issued before
+                    // the transform was slower, the copies competing with the transform's loads)
+#pragma unroll
+                    for (int h = 0; h < 16; h += 8) {
+                        C o[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) o[e] = bold[(size_t)kz_of(q, h + e) * NL + q.line];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const C x = keep[(h + e) * 32 + lane];
+                            const T dx = o[e].x - x.x, dy = o[e].y - x.y;
+                            sm[e & 1][0] += q.wgt * (dx * dx + dy * dy);
+                        }
+                    }
+                }
             }
             Acc<T> acc[5];
 #pragma unroll

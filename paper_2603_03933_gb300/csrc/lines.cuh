@@ -162,6 +162,20 @@ __device__ __forceinline__ void lines_body(const ColArgs<T>& a, int ntiles) {
 
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(ln_nt(M)) k_lines(ColArgs<T> a, int ntiles) { lines_body<T, M, MODE>(a, ntiles); }
+
+// The three line passes of a 3D product on the x-row path -- y forward, z with Lambda / N,
+// y inverse -- as one cooperative launch with two bounded grid barriers: the spectrum is
+// read back right after it was written, while it is still in L2, and two launch boundaries
+// (the drain of one pass's stores and the next launch) become barriers.
+template <typename T, int M>
+__global__ void __launch_bounds__(ln_nt(M)) k_lines3(ColArgs<T> yf, ColArgs<T> zl, ColArgs<T> yi, int ty, int tz,
+                                                     GridBar bar) {
+    lines_body<T, M, C_FWD>(yf, ty);
+    if (!grid_sync_acqrel(bar)) return;
+    lines_body<T, M, C_LAM>(zl, tz);
+    if (!grid_sync_acqrel(bar)) return;
+    lines_body<T, M, C_INV>(yi, ty);
+}
 // many problems of the same size per launch: blockIdx.y selects the problem's arguments
 template <typename T, int M, int MODE>
 __global__ void __launch_bounds__(ln_nt(M)) k_lines_b(const ColArgs<T>* __restrict__ args, int ntiles) {

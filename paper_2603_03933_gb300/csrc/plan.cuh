@@ -118,7 +118,7 @@ public:
 
     static constexpr long long kDefaultBudget = 4000000000LL;   // ~2 s at 2 GHz
 
-    // the argument structs of one hessvec on the x-row path (for batched launches); false elsewhere.
+    // the argument structs of one hessvec on the 2D x-row path (for batched launches); false elsewhere.
     // any_lines: also on grids whose line pass has no persistent k_lines variant (the
     // batched sweep kernel brings its own line tiles)
     bool hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid, int& col_tiles,
@@ -181,7 +181,9 @@ private:
     int hvp3_grid_ = 0;       // CTAs of the fused cooperative product (0: three kernels)
     int imex3_grid_ = 0;      // CTAs of the persistent subproblem kernel (0: not available)
     bool imex3_on_ = true;
+    size_t imex3_smem_ = 0;   // its dynamic shared memory
     int ln_grid_cap_ = 0;     // persistent grid of the pipelined column passes (0: not used)
+    int ln3_grid_ = 0;        // cooperative grid of k_lines3 (3D x-row path products; 0: not used)
     int zf_tpc_ = 0, zf_grid_ = 0, zf_ntiles_ = 0, zf_nbmain_ = 0;
     size_t zf_smem_ = 0;
     bool zf_lines_ = false;   // the fused iteration runs as k_imex_lines (else k_imex_zfused)

@@ -10,7 +10,6 @@
 #include "imex_fused.cuh"
 #include "imex3d.cuh"
 #include "hvp3d.cuh"
-#include "sweep.cuh"
 
 namespace lbtr {
 
@@ -82,11 +81,6 @@ template <typename T, int M> cudaError_t set_lines_attrs(int* per) {
         setl((const void*)k_lines_b<T, M, C_LAM>);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_lines<T, M, C_LAM>, ln_nt(M), ln_smem<T>(M));
-    }
-    if constexpr (M == 512) {
-        cudaError_t r = cudaFuncSetAttribute((const void*)k_lines512_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sw_lines_smem<T>(512));
-        if (r != cudaSuccess) e = r;
     }
     return e;
 }
@@ -206,14 +200,15 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
         if constexpr (sizeof(T) == 4) {
             // the persistent subproblem kernel: every warp owns at most one z-line task, so
             // the grid needs at least NTASKS / 32 CTAs
-            ea = cudaFuncSetAttribute((const void*)k_imex3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)I3_SMEM);
+            const size_t sm3 = I3_SMEM;
+            ea = cudaFuncSetAttribute((const void*)k_imex3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
             if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
             int per3 = 0;
-            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, k_imex3<T>, H3::NT, I3_SMEM);
+            ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, k_imex3<T>, H3::NT, sm3);
             if (ea != cudaSuccess) { err = std::string("cudaOccupancyMaxActiveBlocksPerMultiprocessor: ") + cudaGetErrorString(ea); return 6; }
             const int g3 = nsm * per3;
-            imex3_grid_ = (coop && per3 > 0 && 32 * g3 >= H3::NTASKS) ? g3 : 0;
+            imex3_grid_ = (coop && per3 > 0 && 32 * g3 >= H3::NTASKS && g3 <= I3_MAXG) ? g3 : 0;
+            imex3_smem_ = sm3;
         }
     }
     if (use_planes_) {
@@ -226,6 +221,21 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
         LB_SWITCH_M(m_, ea = set_lines_attrs<T, M>(&per));
         if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
         ln_grid_cap_ = per > 0 ? nsm * per : 0;
+    }
+    if (dim_ == 3 && !use_planes_ && ln_grid_cap_ > 0) {
+        // the three line passes of a 3D product as one cooperative launch (k_lines3)
+        int per = 0, coop = 0;
+        LB_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        LB_SWITCH_M(m_, {
+            if constexpr (M >= 16 && M <= 256) {
+                ea = cudaFuncSetAttribute((const void*)k_lines3<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)ln_smem<T>(M));
+                if (ea == cudaSuccess)
+                    ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lines3<T, M>, ln_nt(M), ln_smem<T>(M));
+            }
+        });
+        if (ea != cudaSuccess) { err = std::string("k_lines3 attributes: ") + cudaGetErrorString(ea); return 6; }
+        ln3_grid_ = (coop && per > 0) ? nsm * per : 0;
     }
 
     int occ = 0;
@@ -584,18 +594,42 @@ template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cud
             return;
         }
     }
+    if (ln3_grid_ > 0) {
+        // 3D on the x-row path: x rows forward, the three line passes in one launch, x rows inverse
+        xfwd(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
+        ColArgs<T> yf, zl, yi;
+        const int ty = col_args(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, nullptr, yf);
+        const int tz = col_args(2, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0,
+                                nullptr, zl);
+        col_args(1, C_INV, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, nullptr, yi);
+        GridBar bar;
+        bar.count = d_bar_; bar.gen = d_bar_ + 32; bar.err = d_err_; bar.budget = budget_; bar.tree = d_bar_ + 64;
+        int ty_ = ty, tz_ = tz;
+        void* args[] = {&yf, &zl, &yi, &ty_, &tz_, &bar};
+        const void* f = nullptr;
+        LB_SWITCH_M(m_, { if constexpr (M >= 16 && M <= 256) f = (const void*)k_lines3<T, M>; });
+        cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
+        cudaError_t e = f ? cudaLaunchCooperativeKernel(f, dim3(ln3_grid_), dim3(ln_nt(m_)), args, ln_smem<T>(m_), s)
+                          : cudaErrorInvalidValue;
+        if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
+        if (prof_) prof_->end(K_COLI, e0, s, 6 * sb());
+        xinv(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
+        return;
+    }
     const int inner = dim_ == 3 ? 2 : 1;
     fwd_outer(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
     cols(inner, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0, s);
     inv_outer(XI_HVP, d_work_, hv, phi, v, slot(S_HVP), (T)1, S_RED0, s);
 }
 
-// The three argument structs of hessvec on the x-row path (2D grids and 3D grids above
-// 128^3), for batched launches of many problems of the same size; false on other paths.
+// The three argument structs of hessvec on the 2D x-row path, for batched launches of many
+// problems of the same size; false on other paths.
 template <typename T>
 bool Plan<T>::hvp_args(const T* phi, const T* v, T* hv, XfArgs<T>& xf, ColArgs<T>& ca, int& col_grid,
                        int& col_tiles, XiArgs<T>& xi, bool any_lines) const {
-    if (use_planes_ || m_ < 16 || (ln_grid_cap_ <= 0 && !any_lines)) return false;
+    // 2D only: a 3D grid on the x-row path also has its y passes, which the batched
+    // launches (rows forward, innermost lines, rows inverse) do not make
+    if (dim_ != 2 || m_ < 16 || (ln_grid_cap_ <= 0 && !any_lines)) return false;
     Plan<T>* self = const_cast<Plan<T>*>(this);
     xf.in = v; xf.phi = phi; xf.g = nullptr; xf.d0 = nullptr; xf.dscale = nullptr;
     xf.main = d_work_; xf.nyq = d_work_ + (size_t)rows_ * h_;
@@ -625,10 +659,6 @@ cudaError_t launch_hvp_batch(int m, int rows, int count, const XfArgs<T>* xf, co
             k_rows_fwd_b<T, M, XF_HVPMEAN><<<gx, 128, rows_smem<T, M>(), s>>>(xf);
             if constexpr (M <= 256) {
                 k_lines_b<T, M, C_LAM><<<dim3((unsigned)col_grid, (unsigned)count), ln_nt(M), ln_smem<T>(M), s>>>(ca, col_tiles);
-            } else if constexpr (M == 512) {
-                // 2D only (the caller groups 512-point problems only in 2D): one Stockham tile per CTA
-                const unsigned tiles = (unsigned)((M / 2 + sw_nl(M) - 1) / sw_nl(M) + 1);
-                k_lines512_b<T><<<dim3(tiles, (unsigned)count), 128, sw_lines_smem<T>(M), s>>>(ca);
             } else {
                 e = cudaErrorInvalidValue;
             }
@@ -837,7 +867,7 @@ int Plan<T>::imex_persistent(const T* phi, const T* g, const T* d0, const double
         void* args[] = {&a};
         cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
         cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_imex3<T>, dim3(imex3_grid_), dim3(H3::NT), args,
-                                                    I3_SMEM, s);
+                                                    imex3_smem_, s);
         if (e != cudaSuccess && launch_err_ == cudaSuccess) launch_err_ = e;
         if (prof_) prof_->end(K_COLI, e0, s, 0.0);
         return 0;

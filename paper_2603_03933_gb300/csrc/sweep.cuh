@@ -236,14 +236,6 @@ __device__ __forceinline__ void sw_lines2d_smem(const ColArgs<T>& a, int tile, u
     }
 }
 
-// The y lines of a group of 2D problems of size 512 as one grouped launch: blockIdx.y picks
-// the problem's argument struct, blockIdx.x one Stockham tile of sw_nl(512) lines.
-template <typename T>
-__global__ void __launch_bounds__(128) k_lines512_b(const ColArgs<T>* __restrict__ args) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    sw_lines2d_smem<T, 512>(args[blockIdx.y], blockIdx.x, smem_raw);
-}
-
 // dispatch a task body over the supported 2D grid sizes
 #define SW_SWITCH_M(mval, ...)                                      \
     switch (mval) {                                                 \
