@@ -128,6 +128,23 @@ lb_status lb_energy_derivs(lb_ctx *ctx, const void *phi, double *out, void *grad
  */
 lb_status lb_hessvec(lb_ctx *ctx, const void *phi, const void *v, void *hv, lb_stream stream);
 
+/*
+ * The same product for fields in HOST memory: count products H v_i at one phi (the way the
+ * Lanczos step and the inner iteration use H), with the copies in and out overlapped with the
+ * products.  The library keeps device staging with the context (phi and three (v, Hv) slots,
+ * allocated on the first call) and two copy streams of its own; the products run on `stream`.
+ *   phi   [in]  host field (copied once per call).
+ *   count [in]  number of products (0: nothing is done).
+ *   v     [in]  host array of `count` host fields (zero mean, not checked).
+ *   hv    [out] host array of `count` host fields; none may alias phi or its v.
+ * Fields are of the context's grid and precision (float for LB_MIXED, double for LB_FP64).
+ * Page-locked host memory lets the copies overlap the products; pageable memory is accepted
+ * and copied synchronously.  Synchronises `stream`: the results are in hv on return.
+ * Errors: LB_ERR_INVALID_ARG (null pointers, negative count, aliasing); LB_ERR_CUDA.
+ */
+lb_status lb_hessvec_host(lb_ctx *ctx, const void *phi, int count, const void *const *v, void *const *hv,
+                          lb_stream stream);
+
 typedef struct {
     double eta;        /* IMEX step size (paper §4: 0.1) */
     double eps_sub;    /* stop when ||g + (H + lambda I) d|| < eps_sub (paper §4: 1e-13) */

@@ -235,6 +235,63 @@ lb_status lb_hessvec(lb_ctx* ctx, const void* phi, const void* v, void* hv, lb_s
     return cuda_check(ctx, "lb_hessvec");
 }
 
+lb_status lb_hessvec_host(lb_ctx* ctx, const void* phi, int count, const void* const* v, void* const* hv,
+                          lb_stream stream) {
+    if (!ctx || !phi || count < 0 || (count > 0 && (!v || !hv)))
+        return fail(ctx, LB_ERR_INVALID_ARG, "lb_hessvec_host: null argument or negative count");
+    for (int i = 0; i < count; ++i) {
+        if (!v[i] || !hv[i]) return fail(ctx, LB_ERR_INVALID_ARG, "lb_hessvec_host: null field pointer");
+        if (hv[i] == phi || hv[i] == v[i]) return fail(ctx, LB_ERR_INVALID_ARG, "lb_hessvec_host: output aliases an input");
+    }
+    if (count == 0) return LB_OK;
+    constexpr int K = lb_ctx::HS_SLOTS;
+    const size_t wsz = ctx->prec == LB_FP64 ? sizeof(double) : sizeof(float);
+    const size_t fb = (size_t)ctx->n() * wsz;
+    const size_t fa = (fb + 255) & ~size_t(255);
+    if (!ctx->hs_base) {
+        if (cudaMalloc(&ctx->hs_base, (1 + 2 * K) * fa) != cudaSuccess) {
+            ctx->hs_base = nullptr;
+            cudaGetLastError();
+            return fail(ctx, LB_ERR_CUDA, "lb_hessvec_host: cudaMalloc of the staging failed");
+        }
+        bool ok = cudaStreamCreateWithFlags(&ctx->hs_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&ctx->hs_out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ctx->hs_phi, cudaEventDisableTiming) == cudaSuccess;
+        for (auto& row : ctx->hs_ev)
+            for (auto& e : row) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return fail(ctx, LB_ERR_CUDA, "lb_hessvec_host: stream or event creation failed");
+    }
+    char* base = static_cast<char*>(ctx->hs_base);
+    void* phi_d = base;
+    auto v_d = [&](int k) { return (void*)(base + (1 + k) * fa); };
+    auto hv_d = [&](int k) { return (void*)(base + (1 + K + k) * fa); };
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t in = ctx->hs_in, out = ctx->hs_out;
+    cudaEvent_t (&ev)[3][K] = ctx->hs_ev;
+    // the copy-in stream starts after everything already on `stream` (the staging's last users)
+    cudaEventRecord(ctx->hs_phi, s);
+    cudaStreamWaitEvent(in, ctx->hs_phi, 0);
+    cudaMemcpyAsync(phi_d, phi, fb, cudaMemcpyHostToDevice, in);
+    for (int i = 0; i < count; ++i) {
+        const int k = i % K;
+        if (i >= K) cudaStreamWaitEvent(in, ev[1][k], 0);        // slot k's v consumed by product i - K
+        cudaMemcpyAsync(v_d(k), v[i], fb, cudaMemcpyHostToDevice, in);
+        cudaEventRecord(ev[0][k], in);
+        cudaStreamWaitEvent(s, ev[0][k], 0);                      // phi (copied first) and v_i in place
+        if (i >= K) cudaStreamWaitEvent(s, ev[2][k], 0);          // slot k's Hv copied out
+        if (ctx->prec == LB_FP64) ctx->p64->hessvec((const double*)phi_d, (const double*)v_d(k), (double*)hv_d(k), s);
+        else ctx->p32->hessvec((const float*)phi_d, (const float*)v_d(k), (float*)hv_d(k), s);
+        cudaEventRecord(ev[1][k], s);
+        cudaStreamWaitEvent(out, ev[1][k], 0);
+        cudaMemcpyAsync(hv[i], hv_d(k), fb, cudaMemcpyDeviceToHost, out);
+        cudaEventRecord(ev[2][k], out);
+    }
+    for (int k = 0; k < K && k < count; ++k) cudaStreamWaitEvent(s, ev[2][k], 0);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(ctx, LB_ERR_CUDA, std::string("lb_hessvec_host: ") + cudaGetErrorString(e));
+    return cuda_check(ctx, "lb_hessvec_host");
+}
+
 lb_status lb_tr_subproblem(lb_ctx* ctx, const void* phi, const void* g, double r, const void* d0,
                            const lb_sub_opts* opts, void* d, lb_sub_info* info, lb_stream stream) {
     if (!ctx || !phi || !g || !d) return fail(ctx, LB_ERR_INVALID_ARG, "lb_tr_subproblem: null argument");

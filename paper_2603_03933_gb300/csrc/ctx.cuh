@@ -28,12 +28,25 @@ struct lb_ctx {
     void* lz_base = nullptr;             // Lanczos basis and its scratch (allocated on first use)
     size_t lz_bytes = 0;
     lbtr::Prof prof;                     // per-kernel-class event timing (profiling aid)
+    // staging of lb_hessvec_host (allocated on first use): phi and HS_SLOTS (v, Hv) slots on
+    // the device, one copy stream per direction, the events that order the slots
+    static constexpr int HS_SLOTS = 3;
+    void* hs_base = nullptr;
+    cudaStream_t hs_in = nullptr, hs_out = nullptr;
+    cudaEvent_t hs_phi = nullptr, hs_ev[3][HS_SLOTS] = {};   // [0] copied in, [1] computed, [2] copied out
 
     ~lb_ctx() {
         delete p64;
         delete p32;
         if (scratch) cudaFree(scratch);
         if (lz_base) cudaFree(lz_base);
+        if (hs_base) cudaFree(hs_base);
+        if (hs_in) cudaStreamDestroy(hs_in);
+        if (hs_out) cudaStreamDestroy(hs_out);
+        if (hs_phi) cudaEventDestroy(hs_phi);
+        for (auto& row : hs_ev)
+            for (auto& e : row)
+                if (e) cudaEventDestroy(e);
     }
 
     long long n() const { return p64->n(); }

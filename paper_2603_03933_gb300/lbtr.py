@@ -114,6 +114,7 @@ SIGNATURES = [
     ("lb_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_profile_read", ctypes.c_int, [_VP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong), _DP]),
     ("lb_set_barrier_budget", ctypes.c_int, [_VP, ctypes.c_longlong]),
+    ("lb_hessvec_host", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("lb_set_persistent_subproblem", ctypes.c_int, [_VP, ctypes.c_int]),
     ("lb_persistent_subproblem_available", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("lb_measure_fp64_rate", ctypes.c_int, [_DP, _VP]),
@@ -276,6 +277,32 @@ def lb_hessvec(ctx: Context, phi, v, hv, stream=None):
                            _stream(stream))
     _check(ctx, st, "lb_hessvec")
     return hv
+
+
+def _host_ptr(ctx: Context, t, name: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a CPU tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype != ctx.dtype:
+        raise TypeError(f"{name} must be {ctx.dtype}, got {t.dtype}")
+    if t.numel() != ctx.npoints:
+        raise ValueError(f"{name} must have {ctx.npoints} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def lb_hessvec_host(ctx: Context, phi, vs, hvs, stream=None):
+    """hvs[i] = H vs[i] for CPU tensors (C: lb_hessvec_host): the copies in and out overlap the
+    products when the tensors are page-locked (tensor.pin_memory()); returns when done."""
+    if len(vs) != len(hvs):
+        raise ValueError("vs and hvs differ in length")
+    n = len(vs)
+    pv = (_VP * max(n, 1))(*[_host_ptr(ctx, v, "v") for v in vs])
+    ph = (_VP * max(n, 1))(*[_host_ptr(ctx, h, "hv") for h in hvs])
+    st = load().lb_hessvec_host(ctx.handle, ctypes.c_void_p(_host_ptr(ctx, phi, "phi")), n, pv, ph, _stream(stream))
+    _check(ctx, st, "lb_hessvec_host")
+    return hvs
 
 
 def default_sub_opts() -> lb_sub_opts:
