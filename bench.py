@@ -631,6 +631,31 @@ def main():
     e2e = {"value": nb * e2e_steps * world / dte, "unit": UNIT,
            "h2d_bytes_per_step": (1 + nb) * field_bytes, "d2h_bytes_per_step": nb * field_bytes,
            "api": "lb_hessvec_host (C ABI, page-locked host fields, copies overlapped with the products)"}
+    # the copies alone: one field in and one out at once on two streams, repeated (the bound
+    # of a product whose input and output cross the host link)
+    try:
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        dst_d, src_d = torch.empty_like(pool[0][1]), pool[0][1]
+
+        def copies():
+            with torch.cuda.stream(sa):
+                dst_d.copy_(v_h[0], non_blocking=True)
+            with torch.cuda.stream(sb):
+                out_h[0].copy_(src_d, non_blocking=True)
+
+        for _ in range(3):
+            copies()
+        torch.cuda.synchronize()
+        reps = 16
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            copies()
+        torch.cuda.synchronize()
+        tc = (time.perf_counter() - t0) / reps
+        e2e["copy_bound"] = {"gbs_bidirectional": 2 * field_bytes / tc / 1e9, "hvp_per_s": 1.0 / tc,
+                             "frac": e2e["value"] / world * tc}
+    except Exception as ex:  # report, do not hide
+        e2e["copy_bound"] = {"error": str(ex)}
 
     # ---- 256^3 at the same settings (context, not the headline) ------------------
     big = None
