@@ -330,8 +330,8 @@ lb_status lb_sis_solve(lb_ctx *ctx, double *phi_inout, const lb_sis_opts *opts, 
  * exits.  Limits: N = n^dim <= 2^18 points (up to 64^3 or 512^2); larger grids return
  * LB_ERR_UNSUPPORTED.  Fields are double for LB_FP64 and float for LB_MIXED.
  * The first call on each device resolves the scratch address and sets kernel
- * attributes (once per device, with that device current); make that first call
- * before any stream capture.  Every call shares the one scratch array: calls that
+ * attributes (once per device, with that device current).  Every call shares the one
+ * scratch array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be serialised
  * by the caller.  Asynchronous on `stream`: each call writes its tables into the scratch
  * with a small kernel and enqueues the transform kernels; it neither copies from the host
