@@ -113,6 +113,6 @@ def test_example2_first_order_flow_ends_at_the_disordered_saddle(lbtr):
     info = lbtr.lb_sis_solve(c, phi, opts=o)
     assert info["status"] == 0 and info["gmax"] < 1e-8
     assert float(phi.abs().max()) < 1e-6 and abs(info["energy"]) < 1e-12
-    lam = lbtr.lb_lambda_min(c, phi)["lambda_min"]
+    lam = lbtr.lb_lambda_min(c, phi, raise_on_noconv=False)["lambda_min"]
     assert abs(lam - ex["tau"]) < 1e-8
 
