@@ -16,8 +16,10 @@
 //                     from the same totals (the Alg. 3 test, the lambda rule of eq.
 //                     lambda_update_rule, a further grid sum per Newton step); b_j stored for
 //                     the next residual, d_{j+1} = b_j / (1 + eta (Lambda + lambda_{j+1})) and
-//                     the inverse z transform into `spec`.  The lines wait in the warp's
-//                     shared scratch across the sums: every warp owns at most one task.
+//                     the inverse z transform into `spec`.  The lines are parked in shared
+//                     memory across the sums (every warp owns at most one task), and the solve
+//                     and inverse with the current multiplier run while the grid sum's barrier
+//                     waits; they are redone only when the rule moves the multiplier.
 //   grid barrier
 // When the test ends the loop at iteration j, the returned iterate d_j = F^{-1}[b_{j-1} /
 // (1 + eta (Lambda + lambda_j))] is formed by one more z step and the planes' inverse and
@@ -62,6 +64,9 @@ template <typename T> struct Imex3Args {
 constexpr size_t I3_SMEM = H3::FSMEM + 32 * 5 * sizeof(double);
 // largest grid the grid sums read in one round (the host launches at most this many CTAs)
 constexpr int I3_MAXG = 256;
+// z-line task warps per CTA; task warp w parks its lines in the scratch of warp w + that
+// count, which has no task (so a grid needs at most 16 task warps per CTA)
+__host__ __device__ constexpr int i3_task_warps(int grid) { return (H3::NTASKS + grid - 1) / grid; }
 
 // phase A on plane z: b = d - eta (g + F''(phi) d), forward x and y transforms into spec
 template <typename T>
@@ -136,6 +141,71 @@ __device__ __forceinline__ bool i3_grid_sum(const GridBar& bar, Part<T>* P, cons
     return true;
 }
 
+// The first half of i3_grid_sum for NQ = 5, split so that work can run between the arrival
+// and the wait: thread 0 publishes the CTA's totals, reads the barrier generation and
+// arrives; the last arrival releases the others.  *gen_out / *last_out: shared results.
+template <typename T>
+__device__ __forceinline__ void i3_publish_arrive(const GridBar& bar, Part<T>* P, const Part<T>* mine,
+                                                  unsigned* gen_out, int* last_out) {
+    if (threadIdx.x == 0) {
+        const int G = gridDim.x;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) P[q * G + blockIdx.x] = mine[q];
+        unsigned* gen = (unsigned*)bar.gen;
+        *gen_out = ld_acquire_gpu(gen);
+        const bool last = atom_add_acq_rel_gpu(bar.count, 1u) == (unsigned)G - 1u;
+        if (last) {
+            *bar.count = 0u;
+            red_add_release_gpu(gen, 1u);
+        }
+        *last_out = last ? 1 : 0;
+    }
+    __syncthreads();
+}
+
+// The second half: thread `waiter` waits (bounded) for the generation to move on, then warp q
+// sums quantity q of all CTAs in a fixed order into out[q] (as i3_grid_sum).  False when the
+// wait gave up (the error flag is set).
+template <typename T>
+__device__ __forceinline__ bool i3_wait_sum(const GridBar& bar, const Part<T>* P, unsigned gen0, int last, int waiter,
+                                            Part<T>* out) {
+    __shared__ int s_ok;
+    if ((int)threadIdx.x == waiter) {
+        s_ok = 1;
+        if (!last) {
+            const unsigned* gen = (const unsigned*)bar.gen;
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(gen) == gen0) {
+                if (clock64() - t0 > bar.budget || *(volatile int*)bar.err != 0) {
+                    atomicCAS(bar.err, 0, 5);
+                    s_ok = 0;
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    const int G = gridDim.x;
+    if ((int)(threadIdx.x >> 5) < 5) {
+        const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        Part<T> x[I3_MAXG / 32];
+#pragma unroll
+        for (int k = 0; k < I3_MAXG / 32; ++k) {
+            if (lane + 32 * k < G) x[k] = part_ldcg(&P[q * G + lane + 32 * k]);
+            else part_zero(x[k]);
+        }
+        Part<T> s = x[0];
+#pragma unroll
+        for (int k = 1; k < I3_MAXG / 32; ++k) s = part_add(s, x[k]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s = part_add(s, part_shfl_down(s, off));
+        if (lane == 0) out[q] = s;
+    }
+    __syncthreads();
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
     using G = H3;
@@ -153,7 +223,7 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
     const int nb = gridDim.x, z = blockIdx.x;
     // The z-line geometry of this thread (its warp's task, the line, the weights) is
     // recomputed where it is used rather than carried through the plane phases, which need
-    // every register.  One task per warp: the host launches at least NTASKS / 32 CTAs.
+    // every register.  One task per warp: the host launches at least NTASKS / 16 CTAs.
     struct Geo {
         int task, line, i;
         bool has, k0line;
@@ -183,6 +253,16 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
         return (T)1 + a.eta * a.xi2 * tt * tt;
     };
     auto scratch = [&]() { return reinterpret_cast<C*>(smem_raw + (threadIdx.x >> 5) * G::ZWARP); };
+    // the lines of b_j parked across the grid sums (lane-private slots), in the z scratch of a
+    // warp without a task: shared memory the plane phase reuses, but not before barrier B
+    auto keepbuf = [&]() {
+        return reinterpret_cast<C*>(smem_raw + (size_t)((threadIdx.x >> 5) + i3_task_warps(nb)) * G::ZWARP);
+    };
+    __shared__ unsigned s_gen;
+    __shared__ int s_last;
+    // the thread that waits at the sums' barrier: one of a warp without a z-line task, so that
+    // the task warps' speculative solve runs during the wait (thread 0 if every warp has one)
+    const int waiter = i3_task_warps(nb) < 32 ? 32 * i3_task_warps(nb) : 0;
     if (threadIdx.x == 0) {
         s_lamp = 0.0;
         s_elp = (T)0;
@@ -225,9 +305,8 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
                     sm[e & 1][3] += qv;
                     sm[e & 1][4] += (T)-2 * eta * qv * rd;
                 }
-                // the lines wait in the warp's scratch (lane-private slots) while the grid sums
-                __syncwarp();
-                C* keep = scratch();
+                // the lines are parked in the warp's keep slots (lane-private) across the grid sums
+                C* keep = keepbuf();
 #pragma unroll
                 for (int e = 0; e < 16; ++e) keep[e * 32 + lane] = v[e];
                 if (check) {
@@ -254,7 +333,23 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
             for (int k = 0; k < 5; ++k) { acc[k].add(sm[0][k]); acc[k].add(sm[1][k]); }
             Part<T> tot[5];
             block_part<T, 5>(acc, red, tot);
-            if (!i3_grid_sum<T, 5>(a.bar, P + (round & 1) * 5 * nb, tot, sh)) return;
+            i3_publish_arrive<T>(a.bar, P + (round & 1) * 5 * nb, tot, &s_gen, &s_last);
+            // while the other CTAs arrive: b_j kept for the next residual, and d_{j+1} solved
+            // with the current multiplier, the most common outcome of the lambda rule (redone
+            // below when the rule moves lambda)
+            if (q.has) {
+                const T ks = a.kscale;
+                const C* keep = keepbuf();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    v[e] = keep[e * 32 + lane];
+                    bnew[(size_t)kz_of(q, e) * NL + q.line] = v[e];
+                    const T f = ks * rcp_t(a_of(q, e) + elp);
+                    v[e] = mk<T>(v[e].x * f, v[e].y * f);
+                }
+                h3_zinv<T>(a.tw, a.spec, q.task, scratch(), v);
+            }
+            if (!i3_wait_sum<T>(a.bar, P + (round & 1) * 5 * nb, s_gen, s_last, waiter, sh)) return;
             ++round;
         }
         if (threadIdx.x == 0) {
@@ -320,7 +415,7 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
             const T el = s_el;
             T sm1[2][2] = {};
             if (q.has) {
-                const C* keep = scratch();
+                const C* keep = keepbuf();
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const C x = keep[e * 32 + (threadIdx.x & 31)];
@@ -349,14 +444,14 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
             st->lam = s_lam;
             st->newton += ns.newton;
         }
-        // ---- b_j kept for the next residual; the diagonal solve; inverse z ----
-        if (q.has) {
+        // ---- the diagonal solve and inverse z again, when the rule moved the multiplier ----
+        // (s_el is bitwise elp whenever lambda_{j+1} = lambda_j: the rule then copies it)
+        if (q.has && s_el != elp) {
             const T el = s_el, ks = a.kscale;
-            const C* keep = scratch();
+            const C* keep = keepbuf();
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                v[e] = keep[e * 32 + (threadIdx.x & 31)];
-                bnew[(size_t)kz_of(q, e) * NL + q.line] = v[e];
+                v[e] = keep[e * 32 + lane];
                 const T f = ks * rcp_t(a_of(q, e) + el);
                 v[e] = mk<T>(v[e].x * f, v[e].y * f);
             }

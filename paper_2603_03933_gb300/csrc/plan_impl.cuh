@@ -198,8 +198,7 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
         LB_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         hvp3_grid_ = (coop && per > 0) ? nsm * per : 0;
         if constexpr (sizeof(T) == 4) {
-            // the persistent subproblem kernel: every warp owns at most one z-line task, so
-            // the grid needs at least NTASKS / 32 CTAs
+            // the persistent subproblem kernel (k_imex3)
             const size_t sm3 = I3_SMEM;
             ea = cudaFuncSetAttribute((const void*)k_imex3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
             if (ea != cudaSuccess) { err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea); return 6; }
@@ -207,7 +206,9 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
             ea = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, k_imex3<T>, H3::NT, sm3);
             if (ea != cudaSuccess) { err = std::string("cudaOccupancyMaxActiveBlocksPerMultiprocessor: ") + cudaGetErrorString(ea); return 6; }
             const int g3 = nsm * per3;
-            imex3_grid_ = (coop && per3 > 0 && 32 * g3 >= H3::NTASKS && g3 <= I3_MAXG) ? g3 : 0;
+            // every warp owns at most one z-line task, and task warps are at most half of the
+            // CTA (each parks its lines in the scratch of a warp without a task)
+            imex3_grid_ = (coop && per3 > 0 && 2 * i3_task_warps(g3) <= 32 && g3 <= I3_MAXG) ? g3 : 0;
             imex3_smem_ = sm3;
         }
     }
