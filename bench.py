@@ -37,8 +37,9 @@ L2_BYTES = 129 * 1024 * 1024
 # ncu DRAM traffic per launch of a kernel class, with the hash of the kernel sources it
 # was captured from (a traffic figure is reported only while those sources match).
 TRAFFIC = {
-    # k_hvp_fused<float> (the whole 128^3 product, one launch)
-    "xfwd": (None, ""),
+    # k_hvp_fused<float> (the whole 128^3 product, one launch): ncu dram__bytes_read.sum +
+    # dram__bytes_write.sum of one cold launch (profiles/hvp_fused_128cubed_mixed_ncu_full.md)
+    "xfwd": (16845824 + 0, "45a59c85a3f3cdf0"),
 }
 
 
