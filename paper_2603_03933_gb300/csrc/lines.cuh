@@ -166,14 +166,43 @@ __global__ void __launch_bounds__(ln_nt(M)) k_lines(ColArgs<T> a, int ntiles) { 
 // The three line passes of a 3D product on the x-row path -- y forward, z with Lambda / N,
 // y inverse -- as one cooperative launch with two bounded grid barriers: the spectrum is
 // read back right after it was written, while it is still in L2, and two launch boundaries
-// (the drain of one pass's stores and the next launch) become barriers.
+// (the drain of one pass's stores and the next launch) become barriers.  The launch also
+// adds up the product's sum of F''(phi) v from the row kernel's per-block partials (rpart,
+// nrpart of them): each CTA a share in the first phase (into l2[blockIdx.x]), CTA 0 the
+// shares in the last, into *msum for the inverse row kernel -- in place of a ticket
+// reduction at the end of the row kernel, whose last block would add thousands of partials
+// on the critical path.  The order of the additions depends only on indices.
 template <typename T, int M>
 __global__ void __launch_bounds__(ln_nt(M)) k_lines3(ColArgs<T> yf, ColArgs<T> zl, ColArgs<T> yi, int ty, int tz,
-                                                     GridBar bar) {
+                                                     GridBar bar, const double* rpart, int nrpart, double* l2,
+                                                     double* msum) {
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < nrpart; i += 32 * gridDim.x) s += __ldcg(&rpart[i]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) l2[blockIdx.x] = s;
+    }
     lines_body<T, M, C_FWD>(yf, ty);
     if (!grid_sync_acqrel(bar)) return;
     lines_body<T, M, C_LAM>(zl, tz);
     if (!grid_sync_acqrel(bar)) return;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        // all loads in flight at once (grids of at most 512 CTAs), then a fixed order
+        constexpr int K = 16;
+        double x[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int i = threadIdx.x + 32 * k;
+            x[k] = i < (int)gridDim.x ? __ldcg(&l2[i]) : 0.0;
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) s += x[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) *msum = s;
+    }
     lines_body<T, M, C_INV>(yi, ty);
 }
 // many problems of the same size per launch: blockIdx.y selects the problem's arguments

@@ -127,8 +127,9 @@ public:
                  const double* lam, int slot, const int* done, ColArgs<T>& a) const;
 
 private:
+    // partials_only: the block sums stay per block (for a later kernel to combine)
     void xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
-              C* spec, int slot, cudaStream_t s, const int* done = nullptr);
+              C* spec, int slot, cudaStream_t s, const int* done = nullptr, bool partials_only = false);
     void xinv(int mode, const C* spec, T* out, const T* phi, const T* v, const double* msum, T oscale,
               int slot, cudaStream_t s, const int* done = nullptr);
     void xmid(int mode, C* spec, const T* phi, const T* g, T scale, cudaStream_t s, const int* done = nullptr);

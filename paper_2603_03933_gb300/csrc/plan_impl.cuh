@@ -236,7 +236,8 @@ int Plan<T>::init(int dim, int m, const double box[3], double xi, double tau, do
             }
         });
         if (ea != cudaSuccess) { err = std::string("k_lines3 attributes: ") + cudaGetErrorString(ea); return 6; }
-        ln3_grid_ = (coop && per > 0) ? nsm * per : 0;
+        // at most 512 CTAs: k_lines3 adds its per-CTA shares with one load round of 16 per lane
+        ln3_grid_ = (coop && per > 0 && nsm * per <= 512) ? nsm * per : 0;
     }
 
     int occ = 0;
@@ -374,12 +375,13 @@ template <typename T> RedSlot Plan<T>::redslot(int slot, int nq, unsigned max_ma
 
 template <typename T>
 void Plan<T>::xfwd(int mode, const T* in, const T* phi, const T* g, const T* d0, const double* dscale,
-                   C* spec, int slot, cudaStream_t s, const int* done) {
+                   C* spec, int slot, cudaStream_t s, const int* done, bool partials_only) {
     XfArgs<T> a;
     a.in = in; a.phi = phi; a.g = g; a.d0 = d0; a.dscale = dscale;
     a.main = spec; a.nyq = spec + (size_t)rows_ * h_;
     a.tw = d_tw_; a.rows = rows_; a.model = model_; a.model.eta = (T)eta;
     a.red = redslot(slot, mode == XF_ENERGY ? 4 : 1, 0u);
+    if (partials_only) a.red.ticket = nullptr;
     a.done = done;
     int grid = (rows_ + x_nl(m_) - 1) / x_nl(m_);
     cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;
@@ -597,7 +599,13 @@ template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cud
     }
     if (ln3_grid_ > 0) {
         // 3D on the x-row path: x rows forward, the three line passes in one launch, x rows inverse
-        xfwd(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s);
+        // the row kernel leaves its sums of F''(phi) v per block; k_lines3 combines them
+        xfwd(XF_HVPMEAN, v, phi, nullptr, nullptr, nullptr, d_work_, S_HVP, s, nullptr, true);
+        int nrp = 0;
+        LB_SWITCH_M(m_, { if constexpr (M >= 16) nrp = rows_grid<T, M>(rows_); });
+        const double* rpart = d_partials_ + (size_t)S_HVP * SLOT_Q * max_blocks_;
+        double* l2 = d_secpart_;
+        double* msum = slot_mut(S_HVP);
         ColArgs<T> yf, zl, yi;
         const int ty = col_args(1, C_FWD, d_work_, nullptr, nullptr, (T)1, 0.0, 0.0, nullptr, S_RED0, nullptr, yf);
         const int tz = col_args(2, C_LAM, d_work_, nullptr, nullptr, (T)(1.0 / (double)n_), 0.0, 0.0, nullptr, S_RED0,
@@ -606,7 +614,7 @@ template <typename T> void Plan<T>::hessvec(const T* phi, const T* v, T* hv, cud
         GridBar bar;
         bar.count = d_bar_; bar.gen = d_bar_ + 32; bar.err = d_err_; bar.budget = budget_; bar.tree = d_bar_ + 64;
         int ty_ = ty, tz_ = tz;
-        void* args[] = {&yf, &zl, &yi, &ty_, &tz_, &bar};
+        void* args[] = {&yf, &zl, &yi, &ty_, &tz_, &bar, &rpart, &nrp, &l2, &msum};
         const void* f = nullptr;
         LB_SWITCH_M(m_, { if constexpr (M >= 16 && M <= 256) f = (const void*)k_lines3<T, M>; });
         cudaEvent_t e0 = prof_ ? prof_->begin(s) : nullptr;

@@ -164,7 +164,7 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 struct RedSlot {
     double* partials;    // [nq][gridDim.x]
     double* result;      // [nq] finalised totals (max for quantities flagged in max_mask)
-    unsigned* ticket;    // zero between launches
+    unsigned* ticket;    // zero between launches; null: write the partials only
     int nq;
     unsigned max_mask;   // bit q set: quantity q is a max, not a sum
 };
@@ -174,6 +174,12 @@ struct RedSlot {
 __device__ __forceinline__ void finalize_partials(const RedSlot& rs, const double* vals) {
     __shared__ int am_last;
     const unsigned G = gridDim.x;
+    if (!rs.ticket) {
+        // partials only: a later kernel combines them
+        if (threadIdx.x == 0)
+            for (int q = 0; q < rs.nq; ++q) rs.partials[q * G + blockIdx.x] = vals[q];
+        return;
+    }
     if (threadIdx.x == 0) {
         for (int q = 0; q < rs.nq; ++q) rs.partials[q * G + blockIdx.x] = vals[q];
         // release: this block's partials before its ticket; acquire: all partials for the last
