@@ -689,6 +689,28 @@ def main():
                                           tr["mixed_per_iteration_launches"]["inner_iters_per_s"])
         for k in ("mixed", "fp64", "mixed_per_iteration_launches"):
             tr[k]["inner_frac_of_hbm"] = tr[k]["inner_alg_gbs"] / peaks["hbm_gbs"]
+    # ---- lambda_min at 128^3 (the second-order test of an SP-II, §1) ------------
+    lam128 = None
+    if args.tr_outer > 0:
+        lam128 = {"workload": "the 128^3 scale field (initial phi), Lanczos to a Ritz residual below 1e-8 "
+                              "(at most 300 steps), default options"}
+        for prec in ("mixed", "fp64"):
+            try:
+                c = lbtr.lb_create_from_array_box(w.shape, w.box, w.xi, w.tau, w.gamma,
+                                                  lbtr.LB_MIXED if prec == "mixed" else lbtr.LB_FP64)
+                ph = torch.tensor(w.phi0, dtype=torch.float32 if prec == "mixed" else torch.float64, device=dev)
+                lbtr.lb_lambda_min(c, ph, raise_on_noconv=False)          # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = lbtr.lb_lambda_min(c, ph, raise_on_noconv=False)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+                lam128[prec] = {"lambda_min": r["lambda_min"], "steps": r["steps"], "converged": r["converged"],
+                                "ritz_residual": r["residual"], "seconds": el,
+                                "ms_per_step": 1e3 * el / max(1, r["steps"])}
+                del c, ph
+            except Exception as ex:  # report, do not hide
+                lam128[prec] = {"error": str(ex)}
     tr_solve = None
     if not args.no_solve:
         try:
@@ -706,9 +728,9 @@ def main():
         cpu = oracle_hvp_rate(M)
 
     # kernels per HVP: one cooperative launch at 128^3 (float); x/y plane pass, z line pass,
-    # inverse plane pass at 32^3-64^3; else x rows, y lines, z lines (with Lambda), y lines,
-    # inverse x rows
-    launches_per_hvp = 1 if M == 128 else 3 if 32 <= M <= 128 else 5
+    # inverse plane pass at 32^3-64^3; else x rows, the three line passes in one cooperative
+    # launch, inverse x rows
+    launches_per_hvp = 1 if M == 128 else 3
     sweep = time_sweep(lbtr, rank, world, args.sweep_instances) if args.sweep_instances > 0 else None
     sweep_solve = None
     if args.sweep_solve_instances > 0:
@@ -726,7 +748,8 @@ def main():
                    "l2": "inputs larger than L2 (rotating pool of 3x L2)", "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": launches_per_hvp * args.batch * args.steps,
-        "fp64": fp64, "size_256": big, "tr": tr, "tr_solve": tr_solve, "sweep": sweep, "sweep_solve": sweep_solve,
+        "fp64": fp64, "size_256": big, "tr": tr, "lambda_min_128": lam128, "tr_solve": tr_solve, "sweep": sweep,
+        "sweep_solve": sweep_solve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
