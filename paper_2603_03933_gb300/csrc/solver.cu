@@ -31,7 +31,7 @@ lb_status lb_ctx::lambda_min(Plan<T>& p, const T* phi, const lb_eig_opts& o, T* 
     const long long len = p.spec_len();
     const int kmax = o.max_steps;
     const int nvec = kmax + 1;
-    const int blk = 256, E = 4;
+    const int blk = 256, E = SPEC_MD_E;
     const int nblk = (int)((len + (long long)blk * E - 1) / ((long long)blk * E));
     // workspace: basis, one work vector, partials, coefficients
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };

@@ -36,24 +36,30 @@ __device__ __forceinline__ T spec_lambda(const SpecGeom& g, long long i, T xi2) 
     return xi2 * t * t;
 }
 
+// Elements per thread of k_spec_multidot: the warp reduction of every vector's sum is paid
+// once per SPEC_MD_E loads, so a larger count amortises it (the kernel is bound by those
+// reductions, not by memory, when it is small).
+constexpr int SPEC_MD_E = 16;
+
 // partials[j][block] = sum over this block's elements of w (/(Lambda + sigma) if minv)
-//                      * Re(conj(Q_j) x), for j < nvec
+//                      * Re(conj(Q_j) x), for j < nvec; a block covers SPEC_MD_E * blockDim.x
+//                      elements
 template <typename T>
 __global__ void k_spec_multidot(const cplx<T>* Q, long long ldq, int nvec, const cplx<T>* x, SpecGeom g,
                                 int minv, T xi2, T sigma, double* partials) {
     extern __shared__ double sred[];       // [nvec][nwarps]
     const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int E = 4;
+    constexpr int E = SPEC_MD_E;
+    auto idx_of = [&](int e) { return ((long long)blockIdx.x * E + e) * blockDim.x + threadIdx.x; };
     cplx<T> xv[E];
     T wv[E];
-    long long idx[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        idx[e] = ((long long)blockIdx.x * E + e) * blockDim.x + threadIdx.x;
-        if (idx[e] < g.len) {
-            xv[e] = x[idx[e]];
-            T w = spec_weight<T>(g, idx[e]);
-            if (minv) w = w / (spec_lambda<T>(g, idx[e], xi2) + sigma);
+        const long long i = idx_of(e);
+        if (i < g.len) {
+            xv[e] = x[i];
+            T w = spec_weight<T>(g, i);
+            if (minv) w = w / (spec_lambda<T>(g, i, xi2) + sigma);
             wv[e] = w;
         } else {
             xv[e] = mk<T>((T)0, (T)0);
@@ -61,15 +67,17 @@ __global__ void k_spec_multidot(const cplx<T>* Q, long long ldq, int nvec, const
         }
     }
     for (int j = 0; j < nvec; ++j) {
-        Acc<T> acc;
         const cplx<T>* q = Q + (long long)j * ldq;
+        // the loads of the E elements first (all in flight), then the products in order
+        cplx<T> av[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            if (idx[e] < g.len) {
-                cplx<T> a = q[idx[e]];
-                acc.add(wv[e] * (a.x * xv[e].x + a.y * xv[e].y));
-            }
+            const long long i = idx_of(e);
+            av[e] = i < g.len ? q[i] : mk<T>((T)0, (T)0);
         }
+        Acc<T> acc;
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc.add(wv[e] * (av[e].x * xv[e].x + av[e].y * xv[e].y));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc.add_shfl(off);
         if (lane == 0) sred[j * nw + warp] = acc.get();
