@@ -730,7 +730,10 @@ def main():
         if M == 128 and "value" in cpu:
             cpu["other_sizes"] = {}
             for m2, secs in ((64, 4.0), (256, 6.0)):
-                r2 = oracle_hvp_rate(m2, seconds=secs)
+                try:
+                    r2 = oracle_hvp_rate(m2, seconds=secs)
+                except Exception as ex:  # report, do not hide
+                    r2 = {"error": str(ex)}
                 cpu["other_sizes"][f"{m2}^3"] = ({"value": r2["value"], "unit": UNIT, "cores": r2["cores"],
                                                   "sample": r2["sample"]} if "value" in r2 else r2)
 
