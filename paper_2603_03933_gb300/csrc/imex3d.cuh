@@ -260,9 +260,10 @@ __global__ void __launch_bounds__(1024, 1) k_imex3(Imex3Args<T> a) {
     };
     __shared__ unsigned s_gen;
     __shared__ int s_last;
-    // the thread that waits at the sums' barrier: one of a warp without a z-line task, so that
-    // the task warps' speculative solve runs during the wait (thread 0 if every warp has one)
-    const int waiter = i3_task_warps(nb) < 32 ? 32 * i3_task_warps(nb) : 0;
+    // the thread that waits at the sums' barrier: the first of the first warp without a z-line
+    // task (the host launches grids with at most 16 task warps per CTA), so that the task
+    // warps' speculative solve runs during the wait
+    const int waiter = 32 * i3_task_warps(nb);
     if (threadIdx.x == 0) {
         s_lamp = 0.0;
         s_elp = (T)0;
