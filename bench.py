@@ -434,9 +434,11 @@ def time_sweep(lbtr, rank: int, world: int, n_instances: int, replays: int = 20)
             "us_per_replay": 1e6 * dt / replays, "instances_per_rank": len(ws), "sizes": sizes,
             "setup_s": setup_s,
             # the tuned strategy: one persistent kernel per replay (and a memset of its queue
-            # heads), or three grouped launches per grid size
+            # heads), or three grouped launches per grid size up to 256^2 and three launches
+            # for each 512^2 instance (a graph branch: no batched line kernel at that size)
             "gpu_launches": (replays if tuning["candidates"][tuning["chosen"]]["strategy"] == "persistent"
-                             else 3 * len(sizes) * replays)}
+                             else replays * (3 * sum(1 for m in sizes if int(m) <= 256) +
+                                             3 * sum(c for m, c in sizes.items() if int(m) > 256)))}
 
 
 def time_sweep_solve(lbtr, rank: int, world: int, n_instances: int, threads: int = 16) -> dict:
